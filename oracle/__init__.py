@@ -1,0 +1,281 @@
+"""FP64 CPU oracle of the scale-based collision-avoidance ADMM (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The arithmetic lives in
+``oca_oracle.c`` (plain C, FP64); this file only compiles it with gcc and
+marshals numpy arrays.  It shares nothing with the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oca_oracle.c")
+_LIB = os.path.join(_HERE, "liboca_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-o", _LIB + ".tmp",
+               _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class OraModel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("dt", C.c_double), ("param", C.c_double * 8),
+                ("Qs", C.c_double * 12), ("Qu", C.c_double * 4)]
+
+
+class OraScene(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_scen", C.c_int), ("fo_max", C.c_int), ("fr_max", C.c_int),
+                ("obs_begin", C.c_void_p), ("obs_nf", C.c_void_p), ("obs_C", C.c_void_p),
+                ("obs_d", C.c_void_p), ("part_begin", C.c_void_p), ("part_nf", C.c_void_p),
+                ("part_link", C.c_void_p), ("part_A", C.c_void_p), ("part_b", C.c_void_p),
+                ("part_off", C.c_void_p), ("horizon", C.c_void_p)]
+
+
+class OraParams(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("eps_pri", C.c_double), ("eps_dual", C.c_double),
+                ("prox", C.c_double), ("max_iter", C.c_int), ("jacobi", C.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            P, I, D = C.c_void_p, C.c_int, C.c_double
+            _lib.ora_scale_lp.argtypes = [I, I, P, P, I, P, P, P, P, P, P]
+            _lib.ora_pair_qp.argtypes = [I, I, P, P, I, P, P, P, D, P, P, P, P, P]
+            _lib.ora_dynamics.argtypes = [P, P, P, P, P, P]
+            _lib.ora_part_pose.argtypes = [P, I, P, P, P, P, P, P]
+            _lib.ora_riccati.argtypes = [I, I, I, P, P, P, P, P, P, P, P, P, P]
+            _lib.ora_cert_margin.argtypes = [I, I, P, P, I, P, P, P, P]
+            _lib.ora_cert_margin.restype = D
+            _lib.ora_scale_batch.argtypes = [P, P, P, P, P, C.c_longlong, P, P, P, P, P, P, P, I]
+            _lib.ora_pair_qp_batch.argtypes = [P, P, P, P, P, P, P, D, C.c_longlong, P, P, P, P, P,
+                                               P, I]
+            _lib.ora_admm_batch.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, I, P, P, P, I]
+            _lib.ora_admm_scenario.argtypes = [P, P, I, P, P, P, P, P, P, P, P]
+            _lib.ora_pair_gn.argtypes = [P, I, I, P, I, P, P, P, P, P, P, P, I, I, D, P, P, P]
+            _lib.ora_num_threads.restype = I
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def make_model(m) -> OraModel:
+    om = OraModel()
+    om.kind = int(m.kind)
+    om.dt = float(m.dt)
+    for i, v in enumerate(m.param):
+        om.param[i] = float(v)
+    for i, v in enumerate(m.Qs):
+        om.Qs[i] = float(v)
+    for i, v in enumerate(m.Qu):
+        om.Qu[i] = float(v)
+    return om
+
+
+class _SceneRef:
+    """Keeps the numpy buffers of an OraScene alive."""
+
+    def __init__(self, scene):
+        self.keep = dict(obs_begin=_i32(scene.obs_begin), obs_nf=_i32(scene.obs_nf),
+                         obs_C=_f64(scene.obs_C), obs_d=_f64(scene.obs_d),
+                         part_begin=_i32(scene.part_begin), part_nf=_i32(scene.part_nf),
+                         part_link=_i32(scene.part_link), part_A=_f64(scene.part_A),
+                         part_b=_f64(scene.part_b), part_off=_f64(scene.part_off),
+                         horizon=_i32(scene.horizon))
+        s = OraScene()
+        s.dim, s.n_scen, s.fo_max, s.fr_max = scene.dim, scene.n_scen, scene.fo_max, scene.fr_max
+        for k, v in self.keep.items():
+            setattr(s, k, v.ctypes.data)
+        self.c = s
+        self.model = make_model(scene.model)
+        self.pair_begin = _i64(scene.pair_begin)
+        self.state_begin = _i64(scene.state_begin)
+        self.ctrl_begin = _i64(scene.ctrl_begin)
+
+
+# ---------------------------------------------------------------------------
+# single-problem entry points
+# ---------------------------------------------------------------------------
+
+def scale_lp(A, b, Cb, db):
+    """alpha*, lambda*, mu*, x* of eqn:scale_opt in the body frame of the part."""
+    A, b, Cb, db = _f64(A), _f64(b), _f64(Cb), _f64(db)
+    d = A.shape[1]
+    lam = np.zeros(len(b))
+    mu = np.zeros(len(db))
+    x = np.zeros(d)
+    al = np.zeros(1)
+    st = lib().ora_scale_lp(d, len(b), _p(A), _p(b), len(db), _p(Cb), _p(db), _p(al), _p(lam),
+                            _p(mu), _p(x))
+    return float(al[0]), lam, mu, x, st
+
+
+def pair_qp(A, b, Cb, db, bq, prox: float = 0.0, ybar=None):
+    """y*, v* = K^T y* + bq, obj = 0.5|v*|^2 of eqn:const_least_square (compact y)."""
+    A, b, Cb, db, bq = _f64(A), _f64(b), _f64(Cb), _f64(db), _f64(bq)
+    d = A.shape[1]
+    ny = len(b) + len(db) + 1
+    yb = _f64(np.zeros(ny) if ybar is None else ybar)
+    y = np.zeros(ny)
+    v = np.zeros(d + 1)
+    obj = np.zeros(1)
+    npiv = np.zeros(1, np.int32)
+    st = lib().ora_pair_qp(d, len(b), _p(A), _p(b), len(db), _p(Cb), _p(db), _p(bq), float(prox),
+                           _p(yb), _p(y), _p(v), _p(obj), _p(npiv))
+    return y, v, float(obj[0]), st
+
+
+def dynamics(model, s, u):
+    """f_c(s,u), df/ds, df/du (continuous time; s_{t+1} = s_t + dt f_c)."""
+    m = make_model(model)
+    s, u = _f64(s), _f64(u)
+    ns, nu = len(s), len(u)
+    f = np.zeros(ns)
+    fs = np.zeros((ns, ns))
+    fu = np.zeros((ns, nu))
+    lib().ora_dynamics(C.byref(m), _p(s), _p(u), _p(f), _p(fs), _p(fu))
+    return f, fs, fu
+
+
+def part_pose(model, link: int, off, s):
+    """rho, R, drho/ds, dR/ds of a robot part."""
+    m = make_model(model)
+    s, off = _f64(s), _f64(off)
+    d = model.dim
+    ns = len(s)
+    rho = np.zeros(d)
+    R = np.zeros((d, d))
+    drho = np.zeros((d, ns))
+    dR = np.zeros((ns, d, d))
+    lib().ora_part_pose(C.byref(m), int(link), _p(off), _p(s), _p(rho), _p(R), _p(drho), _p(dR))
+    return rho, R, drho, dR
+
+
+def riccati(A, B, c, Q, q, R, r, s0):
+    A, B, c, Q, q, R, r, s0 = map(_f64, (A, B, c, Q, q, R, r, s0))
+    N, ns, nu = B.shape[0], B.shape[1], B.shape[2]
+    s = np.zeros((N + 1, ns))
+    u = np.zeros((N, nu))
+    st = lib().ora_riccati(ns, nu, N, _p(A), _p(B), _p(c), _p(Q), _p(q), _p(R), _p(r), _p(s0),
+                           _p(s), _p(u))
+    return s, u, st
+
+
+def pair_gn(model, A, Cw, dd, link, off, s, y_pad, fr_max, fo_max, zeta, xi):
+    """r0 = [T + zeta; R + xi] of one pair at state s and its Jacobian dr/ds
+    (Cw, dd: the obstacle's world-frame halfspaces)."""
+    m = make_model(model)
+    A, Cw, dd, off, s, y_pad, xi = map(_f64, (A, Cw, dd, off, s, y_pad, xi))
+    d = A.shape[1]
+    ns = len(s)
+    rho = np.zeros(d)
+    R = np.zeros((d, d))
+    drho = np.zeros((d, ns))
+    dR = np.zeros((ns, d, d))
+    lib().ora_part_pose(C.byref(m), int(link), _p(off), _p(s), _p(rho), _p(R), _p(drho), _p(dR))
+    r0 = np.zeros(d + 1)
+    J = np.zeros((d + 1, ns))
+    lib().ora_pair_gn(C.byref(m), d, A.shape[0], _p(A), len(dd), _p(Cw), _p(dd), _p(rho), _p(R),
+                      _p(drho), _p(dR), _p(y_pad), int(fr_max), int(fo_max), float(zeta), _p(xi),
+                      _p(r0), _p(J))
+    return r0, J
+
+
+def cert_margin(A, b, Cb, db, lam, mu):
+    A, b, Cb, db, lam, mu = map(_f64, (A, b, Cb, db, lam, mu))
+    return float(lib().ora_cert_margin(A.shape[1], len(b), _p(A), _p(b), len(db), _p(Cb), _p(db),
+                                       _p(lam), _p(mu)))
+
+
+# ---------------------------------------------------------------------------
+# batch entry points over a synthetic scene
+# ---------------------------------------------------------------------------
+
+def scale_batch(scene, states, pairs=None, nthreads: int = 0):
+    """alpha*, lambda*, mu*, x*, certificate margin and status for listed pairs."""
+    sr = _SceneRef(scene)
+    pl = _i64(np.arange(scene.n_pairs) if pairs is None else pairs)
+    n = len(pl)
+    st_arr = _f64(states)
+    alpha = np.zeros(n)
+    lam = np.zeros((n, scene.fr_max))
+    mu = np.zeros((n, scene.fo_max))
+    x = np.zeros((n, scene.dim))
+    margin = np.zeros(n)
+    status = np.zeros(n, np.int32)
+    lib().ora_scale_batch(C.byref(sr.model), C.byref(sr.c), _p(sr.pair_begin), _p(sr.state_begin),
+                          _p(st_arr), n, _p(pl), _p(alpha), _p(lam), _p(mu), _p(x), _p(margin),
+                          _p(status), int(nthreads))
+    return dict(alpha=alpha, lam=lam, mu=mu, x=x, margin=margin, status=status)
+
+
+def pair_qp_batch(scene, states, zeta, xi, y_in, prox: float = 0.0, pairs=None, nthreads: int = 0):
+    """Pair QPs for listed pairs; y_in is pair-major [len(pairs), ny_max]."""
+    sr = _SceneRef(scene)
+    pl = _i64(np.arange(scene.n_pairs) if pairs is None else pairs)
+    n = len(pl)
+    st_arr, z, x, yi = _f64(states), _f64(zeta), _f64(xi), _f64(y_in)
+    y_out = np.zeros((n, scene.ny_max))
+    v = np.zeros((n, scene.dim + 1))
+    obj = np.zeros(n)
+    status = np.zeros(n, np.int32)
+    lib().ora_pair_qp_batch(C.byref(sr.model), C.byref(sr.c), _p(sr.pair_begin), _p(sr.state_begin),
+                            _p(st_arr), _p(z), _p(x), float(prox), n, _p(pl), _p(yi), _p(y_out), _p(v),
+                            _p(obj), _p(status), int(nthreads))
+    return dict(y=y_out, v=v, obj=obj, status=status)
+
+
+def admm_batch(scene, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.0, max_iter=200,
+               jacobi=False, scenarios=None, s=None, u=None, y=None, zeta=None, xi=None,
+               nthreads: int = 0):
+    """Whole ADMM solves; returns the updated state arrays and the report."""
+    sr = _SceneRef(scene)
+    pr = OraParams(float(sigma), float(eps_pri), float(eps_dual), float(prox), int(max_iter),
+                   int(bool(jacobi)))
+    sl = _i32(np.arange(scene.n_scen) if scenarios is None else scenarios)
+    s = _f64(scene.s_init if s is None else s).copy()
+    u = _f64(scene.u_init if u is None else u).copy()
+    y = _f64(scene.cold_y() if y is None else y).copy()
+    zeta = _f64(np.zeros(scene.n_pairs) if zeta is None else zeta).copy()
+    xi = _f64(np.zeros((scene.n_pairs, scene.dim)) if xi is None else xi).copy()
+    report = np.zeros((scene.n_scen, 4))
+    status = np.full(scene.n_scen, -1, np.int32)
+    s_ref = _f64(scene.s_ref)
+    lib().ora_admm_batch(C.byref(sr.model), C.byref(sr.c), C.byref(pr), _p(sr.pair_begin),
+                         _p(sr.state_begin), _p(sr.ctrl_begin), _p(s_ref), _p(s), _p(u), _p(y),
+                         _p(zeta), _p(xi), len(sl), _p(sl), _p(report), _p(status), int(nthreads))
+    return dict(s=s, u=u, y=y, zeta=zeta, xi=xi, iters=report[:, 0].astype(int),
+                r_pri=report[:, 1], r_dual=report[:, 2], cost=report[:, 3], status=status)
+
+
+def num_threads() -> int:
+    return int(lib().ora_num_threads())

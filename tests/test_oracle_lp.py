@@ -1,0 +1,120 @@
+"""Pins of the oracle's scale LP (Sec. III-A eqn:scale_opt, Sec. III-B duality)."""
+import numpy as np
+import pytest
+
+from tests import _pins
+from paper_2406_07048_gb300 import synth
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_alpha_matches_dual_basis_enumeration(ora, dim):
+    rng = np.random.default_rng(11 + dim)
+    for _ in range(60):
+        A, b, C, d = _pins.random_pair(rng, dim)
+        al, lam, mu, x, st = ora.scale_lp(A, b, C, d)
+        assert st == 0
+        ref = _pins.alpha_dual_enum(A, b, C, d)
+        assert al == pytest.approx(ref, rel=1e-10, abs=1e-10)
+
+
+def test_alpha_matches_2d_geometric_brute_force(ora):
+    rng = np.random.default_rng(5)
+    for _ in range(150):
+        A, b, C, d = _pins.random_pair(rng, 2)
+        al = ora.scale_lp(A, b, C, d)[0]
+        assert al == pytest.approx(_pins.alpha_geom_2d(A, b, C, d), rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_alpha_box_box_closed_form(ora, dim):
+    """Axis-aligned box robot |x_i| <= h_i against box obstacle lo <= x <= hi:
+    the gauge is separable, so alpha* = max_i dist(0, [lo_i, hi_i]) / h_i."""
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        h = rng.uniform(0.2, 2.0, dim)
+        A, b = synth.box_halfspaces(h)
+        lo = rng.uniform(-6, 6, dim)
+        hi = lo + rng.uniform(0.1, 3.0, dim)
+        C, d = synth.box_halfspaces(np.ones(dim))
+        d = np.where(np.arange(2 * dim) % 2 == 0, np.repeat(hi, 2), -np.repeat(lo, 2))
+        dist = np.maximum(0, np.maximum(lo, -hi))
+        al = ora.scale_lp(A, b, C, d)[0]
+        assert al == pytest.approx(float(np.max(dist / h)), rel=1e-12, abs=1e-12)
+
+
+def test_alpha_scaling_invariance(ora):
+    """Scaling the robot by c divides alpha* by c."""
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        A, b, C, d = _pins.random_pair(rng, 2)
+        a1 = ora.scale_lp(A, b, C, d)[0]
+        a2 = ora.scale_lp(A, 2.5 * b, C, d)[0]
+        assert a2 == pytest.approx(a1 / 2.5, rel=1e-10, abs=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_strong_duality_and_feasibility(ora, dim):
+    """The returned (lambda, mu) is dual feasible with -d^T mu = alpha*, and
+    the returned x is primal feasible at alpha* (zero primal-dual gap)."""
+    rng = np.random.default_rng(21)
+    for _ in range(60):
+        A, b, C, d = _pins.random_pair(rng, dim)
+        al, lam, mu, x, st = ora.scale_lp(A, b, C, d)
+        assert lam.min() >= -1e-12 and mu.min() >= -1e-12
+        assert b @ lam == pytest.approx(1.0, abs=1e-10)
+        assert np.abs(A.T @ lam + C.T @ mu).max() < 1e-9
+        assert -d @ mu == pytest.approx(al, abs=1e-10)
+        assert np.all(A @ x <= al * b + 1e-9)
+        assert np.all(C @ x <= d + 1e-9)
+
+
+def test_sat_verdict(ora):
+    """alpha* < 1 iff the polygons overlap (separating-axis theorem)."""
+    rng = np.random.default_rng(9)
+    n_checked = 0
+    for _ in range(200):
+        A, b, C, d = _pins.random_pair(rng, 2)
+        al = ora.scale_lp(A, b, C, d)[0]
+        if abs(al - 1.0) < 1e-6:
+            continue
+        assert (al < 1.0) == _pins.sat_overlap_2d(A, b, C, d)
+        n_checked += 1
+    assert n_checked > 150
+
+
+def test_origin_inside_gives_zero(ora):
+    rng = np.random.default_rng(1)
+    A, b, C, d = _pins.random_pair(rng, 2, dist=0.0)
+    assert ora.scale_lp(A, b, C, d)[0] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_batch_matches_single_on_config_poses(ora):
+    """The scene-level driver poses each part (Sec. IV-A y = R x + rho) and
+    transforms the obstacle into the part frame; the result must equal the
+    single-pair LP on C' = C R, d' = d - C rho computed here."""
+    sc = synth.config2()
+    rng = np.random.default_rng(0)
+    st = synth.random_states(sc, rng)
+    pairs = rng.choice(sc.n_pairs, 200, replace=False)
+    r = ora.scale_batch(sc, st, pairs)
+    N = int(sc.horizon[0])
+    for l, p in enumerate(pairs):
+        t = p % N + 1
+        pt = (p // N) % 2
+        j = p // (2 * N)
+        s = st[t]
+        if pt == 0:
+            a = s[2]
+            rho = s[:2] + np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]]) @ sc.part_off[0]
+        else:
+            a = s[4]
+            th = s[2]
+            hitch = s[:2] - sc.model.param[1] * np.array([np.cos(th), np.sin(th)])
+            rho = hitch + np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]]) @ sc.part_off[1]
+        R = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+        nf = sc.obs_nf[j]
+        C = sc.obs_C[j, :nf]
+        d = sc.obs_d[j, :nf]
+        al = ora.scale_lp(sc.part_A[pt], sc.part_b[pt], C @ R, d - C @ rho)[0]
+        assert r["alpha"][l] == pytest.approx(al, rel=1e-12, abs=1e-12)
+        assert r["margin"][l] == pytest.approx(al, rel=1e-8, abs=1e-8)
