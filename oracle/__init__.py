@@ -33,7 +33,8 @@ def build(force: bool = False) -> str:
 
 class OraModel(C.Structure):
     _fields_ = [("kind", C.c_int), ("dt", C.c_double), ("param", C.c_double * 8),
-                ("Qs", C.c_double * 12), ("Qu", C.c_double * 4)]
+                ("Qs", C.c_double * 12), ("Qu", C.c_double * 4), ("s_lo", C.c_double * 12),
+                ("s_hi", C.c_double * 12), ("u_lo", C.c_double * 4), ("u_hi", C.c_double * 4)]
 
 
 class OraScene(C.Structure):
@@ -46,7 +47,8 @@ class OraScene(C.Structure):
 
 class OraParams(C.Structure):
     _fields_ = [("sigma", C.c_double), ("eps_pri", C.c_double), ("eps_dual", C.c_double),
-                ("prox", C.c_double), ("max_iter", C.c_int), ("jacobi", C.c_int)]
+                ("prox", C.c_double), ("max_iter", C.c_int), ("jacobi", C.c_int),
+                ("rho_box", C.c_double), ("damp", C.c_double)]
 
 
 def lib():
@@ -98,6 +100,16 @@ def make_model(m) -> OraModel:
         om.Qs[i] = float(v)
     for i, v in enumerate(m.Qu):
         om.Qu[i] = float(v)
+    for i in range(12):
+        om.s_lo[i], om.s_hi[i] = -1e30, 1e30
+    for i in range(4):
+        om.u_lo[i], om.u_hi[i] = -1e30, 1e30
+    clip = lambda v: float(min(max(v, -1e30), 1e30))
+    for name in ("s_lo", "s_hi", "u_lo", "u_hi"):
+        arr = getattr(m, name, None)
+        if arr is not None:
+            for i, v in enumerate(arr):
+                getattr(om, name)[i] = clip(v)
     return om
 
 
@@ -254,13 +266,13 @@ def pair_qp_batch(scene, states, zeta, xi, y_in, prox: float = 0.0, pairs=None, 
     return dict(y=y_out, v=v, obj=obj, status=status)
 
 
-def admm_batch(scene, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.0, max_iter=200,
+def admm_batch(scene, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1e-2, max_iter=300,
                jacobi=False, scenarios=None, s=None, u=None, y=None, zeta=None, xi=None,
-               nthreads: int = 0):
+               nthreads: int = 0, rho_box=100.0, damp=100.0):
     """Whole ADMM solves; returns the updated state arrays and the report."""
     sr = _SceneRef(scene)
     pr = OraParams(float(sigma), float(eps_pri), float(eps_dual), float(prox), int(max_iter),
-                   int(bool(jacobi)))
+                   int(bool(jacobi)), float(rho_box), float(damp))
     sl = _i32(np.arange(scene.n_scen) if scenarios is None else scenarios)
     s = _f64(scene.s_init if s is None else s).copy()
     u = _f64(scene.u_init if u is None else u).copy()

@@ -14,7 +14,8 @@
  *                     elimination of one lambda (eqn:const_least_square_ineq),
  *                     KKT -> LCP (eqn:kkt_conditions,
  *                     eqn:linear_complementarity_problem), Lemke's method.
- *                     Optional proximal term 0.5*prox*|y - ybar|^2.
+ *                     Optional proximal term 0.5*prox*sum_i |K_i|^2 (y_i - ybar_i)^2
+ *                     (each generator's step measured in residual space).
  *   ora_dynamics      Sec. IV-A eqn:system_eqn, s_{t+1} = s_t + dt*f_c(s,u).
  *   ora_part_pose     rho(s), R(s) of Sec. IV-A and their state derivatives.
  *   ora_riccati       the step-2 LQ subproblem (SQP: one QP per iteration,
@@ -205,18 +206,32 @@ int ora_scale_lp(int d, int nr, const double *A, const double *b, int no, const 
 /* ------------------------------------------------------------------------ */
 
 /* Lemke's method for w = M z + q, w,z >= 0, w^T z = 0.  n <= ORA_MAXL.
+ * Degenerate LCPs (many optimal y of the pair QP) make floating-point
+ * pivoting fragile, so the pivots are chosen on q + delta, with delta a
+ * fixed generic perturbation of relative size 1e-9 (a numerical stand-in for
+ * the symbolic lexicographic perturbation), and the solution is then
+ * recomputed exactly from the final complementary basis with the original q:
+ * x_B = B^{-1} q, B^{-1} being the w-columns of the tableau.
  * Returns 0 solved, 1 ray termination, 2 pivot cap. */
-static int ora_lemke(int n, const double *M, const double *q, double *z, int *npiv) {
+static int ora_lemke(int n, const double *M, const double *q_in, double *z, int *npiv) {
     const int cols = 2 * n + 2;          /* w(n) | z(n) | z0 | rhs */
     const int cz0 = 2 * n, crhs = 2 * n + 1;
     static __thread double T[ORA_MAXL * (2 * ORA_MAXL + 2)];
     int basis[ORA_MAXL];
     const double eps = 1e-13;
+    double q[ORA_MAXL], qmax = 0.0;
     *npiv = 0;
     int neg = 0;
-    for (int i = 0; i < n; ++i) if (q[i] < 0.0) neg = 1;
+    for (int i = 0; i < n; ++i) {
+        if (q_in[i] < 0.0) neg = 1;
+        qmax = fmax(qmax, fabs(q_in[i]));
+    }
     for (int i = 0; i < n; ++i) z[i] = 0.0;
     if (!neg) return 0;
+    for (int i = 0; i < n; ++i) {
+        const double frac = fmod(0.6180339887498949 * (i + 1), 1.0);
+        q[i] = q_in[i] + 1e-9 * (1.0 + qmax) * (0.5 + frac);
+    }
     memset(T, 0, sizeof(double) * n * cols);
     for (int i = 0; i < n; ++i) {
         T[i * cols + i] = 1.0;
@@ -225,37 +240,47 @@ static int ora_lemke(int n, const double *M, const double *q, double *z, int *np
         T[i * cols + crhs] = q[i];
         basis[i] = i;
     }
-    /* initial pivot: z0 enters, the row of the most negative q_i leaves */
+    /* initial pivot: z0 enters, the row of the most negative q_i leaves
+     * (largest index among ties keeps the tableau lexicographically positive) */
     int r = 0;
-    for (int i = 1; i < n; ++i) if (q[i] < q[r]) r = i;
+    for (int i = 1; i < n; ++i) if (q[i] <= q[r]) r = i;
     int leaving = basis[r];
     ora_pivot(T, n, cols, r, cz0);
     basis[r] = cz0;
     *npiv = 1;
     for (int it = 0; it < 50 * n + 50; ++it) {
         int enter = (leaving < n) ? leaving + n : leaving - n;   /* complement */
-        /* lexicographic minimum-ratio test on rows with positive entry */
-        int rr = -1;
+        /* lexicographic minimum-ratio test: minimum ratio over rows with a
+         * positive entry, then filter the tie set column by column of B^{-1}
+         * (the w columns), preferring z0 when it is tied */
+        double cmax = 0.0;
+        for (int i = 0; i < n; ++i) cmax = fmax(cmax, fabs(T[i * cols + enter]));
+        const double atol = eps * (1.0 + cmax);
+        double th = INFINITY;
         for (int i = 0; i < n; ++i) {
             double a = T[i * cols + enter];
-            if (a <= eps) continue;
-            if (rr < 0) { rr = i; continue; }
-            double ai = a, ar = T[rr * cols + enter];
-            double ri = T[i * cols + crhs] / ai, rb = T[rr * cols + crhs] / ar;
-            int better = 0;
-            if (ri < rb - 1e-14 * (1.0 + fabs(rb))) better = 1;
-            else if (ri <= rb + 1e-14 * (1.0 + fabs(rb))) {
-                if (basis[i] == cz0) better = 1;            /* let z0 leave first */
-                else if (basis[rr] == cz0) better = 0;
-                else {
-                    for (int k = 0; k < n; ++k) {          /* columns of B^{-1} */
-                        double ci = T[i * cols + k] / ai, cr = T[rr * cols + k] / ar;
-                        if (ci < cr - 1e-14) { better = 1; break; }
-                        if (ci > cr + 1e-14) break;
-                    }
-                }
+            if (a > atol) th = fmin(th, T[i * cols + crhs] / a);
+        }
+        int rr = -1;
+        if (th < INFINITY) {
+            int cand[ORA_MAXL], nc = 0;
+            const double ttol = 1e-12 * (1.0 + fabs(th));
+            for (int i = 0; i < n; ++i) {
+                double a = T[i * cols + enter];
+                if (a > atol && T[i * cols + crhs] / a <= th + ttol) cand[nc++] = i;
             }
-            if (better) rr = i;
+            for (int c = 0; c < nc; ++c)
+                if (basis[cand[c]] == cz0) rr = cand[c];
+            for (int k = 0; rr < 0 && k < n && nc > 1; ++k) {
+                double mn = INFINITY;
+                for (int c = 0; c < nc; ++c) mn = fmin(mn, T[cand[c] * cols + k] / T[cand[c] * cols + enter]);
+                const double ktol = 1e-12 * (1.0 + fabs(mn));
+                int m2 = 0;
+                for (int c = 0; c < nc; ++c)
+                    if (T[cand[c] * cols + k] / T[cand[c] * cols + enter] <= mn + ktol) cand[m2++] = cand[c];
+                nc = m2;
+            }
+            if (rr < 0) rr = cand[0];
         }
         if (rr < 0) return 1;
         leaving = basis[rr];
@@ -263,8 +288,18 @@ static int ora_lemke(int n, const double *M, const double *q, double *z, int *np
         basis[rr] = enter;
         ++*npiv;
         if (leaving == cz0) {
+            /* exact resolve with the unperturbed q on the final basis */
+            int ok = 1;
+            double xb[ORA_MAXL];
+            for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int k = 0; k < n; ++k) acc += T[i * cols + k] * q_in[k];
+                xb[i] = acc;
+                if (acc < -1e-9 * (1.0 + qmax)) ok = 0;
+            }
             for (int i = 0; i < n; ++i)
-                if (basis[i] >= n && basis[i] < 2 * n) z[basis[i] - n] = T[i * cols + crhs];
+                if (basis[i] >= n && basis[i] < 2 * n)
+                    z[basis[i] - n] = ok ? fmax(0.0, xb[i]) : T[i * cols + crhs];
             return 0;
         }
     }
@@ -304,14 +339,24 @@ int ora_pair_qp(int d, int nr, const double *A, const double *b, int no, const d
     }
     for (int c = 0; c < V; ++c) bt[c] = bq[c] + K[e * V + c] * eta / ke;  /* b~ */
     const double etat = eta / ke;                                     /* eta~ */
-    /* LCP of size n+1: M = [[H, kt], [-kt^T, 0]], q = [f; eta~] */
+    /* LCP of size n+1: M = [[H, kt], [-kt^T, 0]], q = [f; eta~].
+     * The proximal term is measured in residual space:
+     * 0.5 prox sum_i |K_i|^2 (y_i - ybar_i)^2 = 0.5 prox (y - ybar)^T Dg (y - ybar),
+     * which with y = y_0 + N y_u adds prox N^T Dg N to H and
+     * prox N^T Dg (y_0 - ybar) to f. */
+    double Dg[ORA_MAXY];
+    for (int i = 0; i < ny; ++i) {
+        double s2 = 0.0;
+        for (int c = 0; c < V; ++c) s2 += K[i * V + c] * K[i * V + c];
+        Dg[i] = s2;
+    }
     const int L = n + 1;
     double M[ORA_MAXL * ORA_MAXL], q[ORA_MAXL], z[ORA_MAXL];
     for (int a = 0; a < n; ++a) {
         for (int c2 = 0; c2 < n; ++c2) {
             double s = 0.0;
             for (int c = 0; c < V; ++c) s += Kt[a * V + c] * Kt[c2 * V + c];
-            if (prox > 0.0) s += prox * ((a == c2 ? 1.0 : 0.0) + kt[a] * kt[c2]);
+            if (prox > 0.0) s += prox * ((a == c2 ? Dg[uidx[a]] : 0.0) + Dg[e] * kt[a] * kt[c2]);
             M[a * L + c2] = s;
         }
         M[a * L + n] = kt[a];
@@ -320,7 +365,7 @@ int ora_pair_qp(int d, int nr, const double *A, const double *b, int no, const d
         for (int c = 0; c < V; ++c) f += Kt[a * V + c] * bt[c];
         if (prox > 0.0) {
             double yb_e = ybar ? ybar[e] : 0.0, yb_a = ybar ? ybar[uidx[a]] : 0.0;
-            f += prox * (-kt[a] * (etat - yb_e) - yb_a);
+            f += prox * (-Dg[e] * kt[a] * (etat - yb_e) - Dg[uidx[a]] * yb_a);
         }
         q[a] = f;
     }
@@ -356,6 +401,8 @@ typedef struct {
     double dt;
     double param[8];
     double Qs[ORA_MAXS], Qu[ORA_MAXU];
+    double s_lo[ORA_MAXS], s_hi[ORA_MAXS];  /* state boxes of eqn:MPC_opt_origin (+-1e30: none) */
+    double u_lo[ORA_MAXU], u_hi[ORA_MAXU];  /* control boxes */
 } ora_model;
 
 static int ora_ns(int kind) { return kind == 0 ? 4 : kind == 1 ? 5 : 12; }
@@ -401,29 +448,29 @@ void ora_dynamics(const ora_model *md, const double *s, const double *u, double 
     memset(Fs, 0, sizeof(Fs));
     memset(Fu, 0, sizeof(Fu));
     if (md->kind == 0 || md->kind == 1) {
-        const double L = md->param[0];
-        double th = s[2], v = s[3], a = u[0], dl = u[1];
-        double tn = tan(dl), sec2 = 1.0 + tn * tn;
+        /* kinematic bicycle with the steering entered as path curvature
+         * kappa = tan(delta) / L:  x' = v cos th, y' = v sin th, th' = v kappa, v' = a */
+        double th = s[2], v = s[3], a = u[0], kap = u[1];
         F[0] = v * cos(th);
         F[1] = v * sin(th);
-        F[2] = v * tn / L;
+        F[2] = v * kap;
         F[3] = a;
         Fs[0 * ns + 2] = -v * sin(th); Fs[0 * ns + 3] = cos(th);
         Fs[1 * ns + 2] = v * cos(th);  Fs[1 * ns + 3] = sin(th);
-        Fs[2 * ns + 3] = tn / L;
-        Fu[2 * nu + 1] = v * sec2 / L;
+        Fs[2 * ns + 3] = kap;
+        Fu[2 * nu + 1] = v;
         Fu[3 * nu + 0] = 1.0;
         if (md->kind == 1) {
-            /* off-axle hitch: hitch M behind the rear axle, trailer axle L2 behind hitch:
-             * psi_dot = (v/L2) sin(th-psi) - (v M tan(dl)/(L L2)) cos(th-psi) */
+            /* off-axle hitch M behind the rear axle, trailer axle L2 behind the hitch:
+             * psi' = (v/L2) sin(th-psi) - (v M kappa / L2) cos(th-psi) */
             const double Mh = md->param[1], L2 = md->param[2];
             double ps = s[4], sd = sin(th - ps), cd = cos(th - ps);
-            F[4] = v / L2 * sd - v * Mh * tn / (L * L2) * cd;
-            double dth = v / L2 * cd + v * Mh * tn / (L * L2) * sd;
+            F[4] = v / L2 * sd - v * Mh * kap / L2 * cd;
+            double dth = v / L2 * cd + v * Mh * kap / L2 * sd;
             Fs[4 * ns + 2] = dth;
             Fs[4 * ns + 4] = -dth;
-            Fs[4 * ns + 3] = sd / L2 - Mh * tn / (L * L2) * cd;
-            Fu[4 * nu + 1] = -v * Mh * sec2 / (L * L2) * cd;
+            Fs[4 * ns + 3] = sd / L2 - Mh * kap / L2 * cd;
+            Fu[4 * nu + 1] = -v * Mh / L2 * cd;
         }
     } else {
         const double m = md->param[0], g = md->param[1];
@@ -654,6 +701,8 @@ typedef struct {
     double sigma, eps_pri, eps_dual, prox;
     int max_iter;
     int jacobi;        /* 1: literal superscript-k (Jacobi) reading of steps 2 and 3 */
+    double rho_box;    /* penalty of the box-constraint block (state/control bounds); 0: off */
+    double damp;       /* proximal weight 0.5*damp*|(s,u) - (s,u)^k|^2 in step 2      */
 } ora_admm_params;
 
 /* Transform obstacle j into the body frame of a part with pose (rho, R):
@@ -759,6 +808,15 @@ int ora_admm_scenario(const ora_model *md, const ora_scene *sc, int scen, const 
     double *rq = (double *)calloc((size_t)N * nu, sizeof(double));
     double *sn = (double *)malloc(sizeof(double) * (N + 1) * ns);
     double *un = (double *)malloc(sizeof(double) * N * nu);
+    /* box block: bounded copies z and scaled duals w of the states and controls */
+    double *zs = (double *)malloc(sizeof(double) * (N + 1) * ns), *ws = (double *)calloc((size_t)(N + 1) * ns, sizeof(double));
+    double *zu = (double *)malloc(sizeof(double) * N * nu), *wu = (double *)calloc((size_t)N * nu, sizeof(double));
+    for (int t = 0; t <= N; ++t)
+        for (int i = 0; i < ns; ++i)
+            zs[(size_t)t * ns + i] = fmin(fmax(s[(size_t)t * ns + i], md->s_lo[i]), md->s_hi[i]);
+    for (int t = 0; t < N; ++t)
+        for (int i = 0; i < nu; ++i)
+            zu[(size_t)t * nu + i] = fmin(fmax(u[(size_t)t * nu + i], md->u_lo[i]), md->u_hi[i]);
     for (it = 0; it < pr->max_iter; ++it) {
         /* ---- step 1: pair QPs at s^k ---- */
         rd = 0.0;
@@ -821,6 +879,13 @@ int ora_admm_scenario(const ora_model *md, const ora_scene *sc, int scen, const 
             for (int i = 0; i < nu; ++i) {
                 for (int k = 0; k < nu; ++k) Rq[(size_t)t * nu * nu + i * nu + k] = (i == k) ? 2.0 * md->Qu[i] : 0.0;
                 rq[(size_t)t * nu + i] = 0.0;
+                /* proximal damping and the box block's augmented term */
+                Rq[(size_t)t * nu * nu + i * nu + i] += pr->damp;
+                rq[(size_t)t * nu + i] -= pr->damp * ut[i];
+                if (md->u_lo[i] > -1e29 || md->u_hi[i] < 1e29) {
+                    Rq[(size_t)t * nu * nu + i * nu + i] += pr->rho_box;
+                    rq[(size_t)t * nu + i] -= pr->rho_box * (zu[(size_t)t * nu + i] - wu[(size_t)t * nu + i]);
+                }
             }
         }
         for (int t = 0; t <= N; ++t) {
@@ -829,6 +894,14 @@ int ora_admm_scenario(const ora_model *md, const ora_scene *sc, int scen, const 
             for (int i = 0; i < ns; ++i) {
                 for (int k = 0; k < ns; ++k) Qt[i * ns + k] = (i == k) ? 2.0 * md->Qs[i] : 0.0;
                 qt[i] = -2.0 * md->Qs[i] * sr[i];
+                if (t >= 1) {
+                    Qt[i * ns + i] += pr->damp;
+                    qt[i] -= pr->damp * s[(size_t)t * ns + i];
+                    if (md->s_lo[i] > -1e29 || md->s_hi[i] < 1e29) {
+                        Qt[i * ns + i] += pr->rho_box;
+                        qt[i] -= pr->rho_box * (zs[(size_t)t * ns + i] - ws[(size_t)t * ns + i]);
+                    }
+                }
             }
         }
         for (int t = 1; t <= N; ++t) {
@@ -876,9 +949,32 @@ int ora_admm_scenario(const ora_model *md, const ora_scene *sc, int scen, const 
             status = ORA_FAIL;
             break;
         }
+        /* ---- box block: z = clip((s,u)^{k+1} + w), w += (s,u)^{k+1} - z ---- */
+        double rpb = 0.0, rdb = 0.0;
+        for (int t = 1; t <= N && pr->rho_box > 0.0; ++t)
+            for (int i = 0; i < ns; ++i) {
+                if (!(md->s_lo[i] > -1e29 || md->s_hi[i] < 1e29)) continue;
+                const size_t k2 = (size_t)t * ns + i;
+                const double zn = fmin(fmax(sn[k2] + ws[k2], md->s_lo[i]), md->s_hi[i]);
+                rdb += (zn - zs[k2]) * (zn - zs[k2]);
+                zs[k2] = zn;
+                ws[k2] += sn[k2] - zn;
+                rpb += (sn[k2] - zn) * (sn[k2] - zn);
+            }
+        for (int t = 0; t < N && pr->rho_box > 0.0; ++t)
+            for (int i = 0; i < nu; ++i) {
+                if (!(md->u_lo[i] > -1e29 || md->u_hi[i] < 1e29)) continue;
+                const size_t k2 = (size_t)t * nu + i;
+                const double zn = fmin(fmax(un[k2] + wu[k2], md->u_lo[i]), md->u_hi[i]);
+                rdb += (zn - zu[k2]) * (zn - zu[k2]);
+                zu[k2] = zn;
+                wu[k2] += un[k2] - zn;
+                rpb += (un[k2] - zn) * (un[k2] - zn);
+            }
         /* ---- step 3: zeta += T(s^{k+1}, y^{k+1}), xi += R(s^{k+1}, y^{k+1}) ---- */
         const double *s3 = pr->jacobi ? s : sn;
-        rp = 0.0;
+        rp = rpb;
+        rd += rdb;
         for (int j = 0; j < M; ++j) {
             const int gm = m0 + j, no = sc->obs_nf[gm];
             const double *C = sc->obs_C + (size_t)gm * FO * d, *dd = sc->obs_d + (size_t)gm * FO;
@@ -916,7 +1012,7 @@ int ora_admm_scenario(const ora_model *md, const ora_scene *sc, int scen, const 
     out[2] = rd;
     out[3] = F;
     free(ynew); free(Aq); free(Bq); free(cq); free(Qq); free(qq); free(Rq); free(rq);
-    free(sn); free(un);
+    free(sn); free(un); free(zs); free(ws); free(zu); free(wu);
     return status;
 }
 

@@ -51,6 +51,10 @@ class Model:
     param: np.ndarray   # bicycle: [L]; trailer: [L, M, L2]; quad: [m, g, Jx, Jy, Jz, ell, km]
     Qs: np.ndarray      # diagonal state weights (n_s)
     Qu: np.ndarray      # diagonal control weights (n_u)
+    s_lo: np.ndarray = None   # state box of the MPC problem (-inf/inf: none)
+    s_hi: np.ndarray = None
+    u_lo: np.ndarray = None   # control box
+    u_hi: np.ndarray = None
 
     @property
     def ns(self) -> int:
@@ -158,23 +162,38 @@ class Scene:
 # model constants (documented readings: the paper gives none except dt, sigma)
 # ---------------------------------------------------------------------------
 
+INF = float("inf")
+
+
+KAPPA_MAX = math.tan(0.6) / 2.7   # curvature of a 0.6 rad steering angle, wheelbase 2.7 m
+
+
 def bicycle_model(dt: float = 0.1) -> Model:
+    # controls: acceleration and path curvature kappa = tan(steer) / L;
+    # speed in [0, 30] m/s, acceleration in [-6, 6] m/s^2, |steer| <= 0.6 rad
     return Model(MODEL_BICYCLE, dt, np.array([2.7]), np.array([1.0, 1.0, 0.1, 0.1]),
-                 np.array([0.1, 0.1]))
+                 np.array([0.1, 10.0]), np.array([-INF, -INF, -INF, 0.0]), np.array([INF, INF, INF, 30.0]),
+                 np.array([-6.0, -KAPPA_MAX]), np.array([6.0, KAPPA_MAX]))
 
 
 def trailer_model(dt: float = 0.1) -> Model:
     # wheelbase 2.7 m, hitch 1 m behind the rear axle, hitch->trailer axle 5 m
     return Model(MODEL_TRAILER, dt, np.array([2.7, 1.0, 5.0]),
-                 np.array([1.0, 1.0, 0.1, 0.1, 0.1]), np.array([0.1, 0.1]))
+                 np.array([1.0, 1.0, 0.1, 0.1, 0.1]), np.array([0.1, 10.0]),
+                 np.array([-INF, -INF, -INF, 0.0, -INF]), np.array([INF, INF, INF, 30.0, INF]),
+                 np.array([-6.0, -KAPPA_MAX]), np.array([6.0, KAPPA_MAX]))
 
 
 def quad_model(dt: float = 0.1) -> Model:
     # m = 1 kg, J = diag(0.01, 0.01, 0.02), arm 0.25 m, yaw-torque coeff 0.016;
-    # controls are rotor thrusts relative to hover (m g / 4 each)
+    # controls are rotor thrusts relative to hover (m g / 4 each), each rotor
+    # thrust within [0, 3 m g / 4]; roll and pitch within +-0.8 rad
+    hover = 9.81 / 4
     return Model(MODEL_QUAD, dt, np.array([1.0, 9.81, 0.01, 0.01, 0.02, 0.25, 0.016]),
                  np.array([1.0, 1.0, 1.0, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.01, 0.01, 0.01]),
-                 np.array([0.05, 0.05, 0.05, 0.05]))
+                 np.array([0.05, 0.05, 0.05, 0.05]),
+                 np.array([-INF] * 6 + [-0.8, -0.8] + [-INF] * 4), np.array([INF] * 6 + [0.8, 0.8] + [INF] * 4),
+                 np.full(4, -hover), np.full(4, 2 * hover))
 
 
 # ---------------------------------------------------------------------------
@@ -335,10 +354,13 @@ def config1() -> Scene:
     return _assemble(model, [sc], "plain-2d-bicycle-N20-M4")
 
 
-def _trailer_scen(rng, model, N, n_obs, fmin, fmax, length, width, n_parts):
-    keep = [np.array([0.0, width / 2]), np.array([length, width / 2])]
+def _trailer_scen(rng, model, N, n_obs, fmin, fmax, length, width, n_parts, v_ref=10.0):
+    """Obstacles over length x width; the reference runs along the centre line
+    at v_ref (the horizon covers min(length, v_ref N dt) of it)."""
+    reach = min(length, v_ref * N * model.dt)
+    keep = [np.array([0.0, width / 2]), np.array([reach, width / 2])]
     obs = _place_2d(rng, n_obs, fmin, fmax, 0.0, length, 0.0, width, keep, 8.0)
-    ref = _ref_2d(model, N, 0.0, length, width / 2)
+    ref = _ref_2d(model, N, 0.0, reach, width / 2)
     parts = [_tractor(), _trailer()][:n_parts]
     return _Scen(obs, parts, N, ref, np.zeros((N, model.nu)))
 

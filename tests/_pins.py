@@ -170,10 +170,12 @@ def qp_brute_prox0(K, kappa, bq):
 
 
 def qp_brute_prox(K, kappa, bq, prox, ybar):
-    """min 0.5|K^T y + bq|^2 + 0.5 prox |y - ybar|^2 s.t. kappa^T y = 1,
-    y >= 0 (strictly convex): the minimum over every face {y_i = 0, i not
-    in F} of the face's equality-constrained minimiser, when feasible."""
+    """min 0.5|K^T y + bq|^2 + 0.5 prox sum_i |K_i|^2 (y_i - ybar_i)^2
+    s.t. kappa^T y = 1, y >= 0 (strictly convex): the minimum over every
+    face {y_i = 0, i not in F} of the face's equality-constrained
+    minimiser, when feasible."""
     n, V = K.shape
+    Dg = (K ** 2).sum(axis=1)
     best, best_y = np.inf, None
     for k in range(1, n + 1):
         for F in itertools.combinations(range(n), k):
@@ -182,10 +184,10 @@ def qp_brute_prox(K, kappa, bq, prox, ybar):
                 continue
             G = K[F]
             M = np.zeros((k + 1, k + 1))
-            M[:k, :k] = G @ G.T + prox * np.eye(k)
+            M[:k, :k] = G @ G.T + prox * np.diag(Dg[F])
             M[:k, k] = kappa[F]
             M[k, :k] = kappa[F]
-            rhs = np.concatenate([-G @ bq + prox * ybar[F], [1.0]])
+            rhs = np.concatenate([-G @ bq + prox * Dg[F] * ybar[F], [1.0]])
             sol = np.linalg.solve(M, rhs)
             yF = sol[:k]
             if np.any(yF < -1e-12):
@@ -193,7 +195,7 @@ def qp_brute_prox(K, kappa, bq, prox, ybar):
             y = np.zeros(n)
             y[F] = yF
             v = K.T @ y + bq
-            o = 0.5 * float(v @ v) + 0.5 * prox * float((y - ybar) @ (y - ybar))
+            o = 0.5 * float(v @ v) + 0.5 * prox * float(Dg @ (y - ybar) ** 2)
             if o < best:
                 best, best_y = o, y
     return best, best_y
@@ -202,10 +204,11 @@ def qp_brute_prox(K, kappa, bq, prox, ybar):
 def qp_kkt_residual(K, kappa, bq, y, prox=0.0, ybar=None):
     """Largest violation of the KKT conditions of the pair QP at y:
     primal feasibility, and g + nu kappa >= 0 with complementarity, where
-    g = K (K^T y + bq) + prox (y - ybar) and nu is fitted on the support."""
+    g = K (K^T y + bq) + prox Dg (y - ybar), Dg = |K_i|^2, and nu is fitted
+    on the support."""
     g = K @ (K.T @ y + bq)
     if prox > 0:
-        g = g + prox * (y - ybar)
+        g = g + prox * (K ** 2).sum(axis=1) * (y - ybar)
     sup = [i for i in range(len(y)) if y[i] > 1e-9 and kappa[i] > 0]
     nu = -np.mean([g[i] / kappa[i] for i in sup]) if sup else -np.min(g[kappa > 0] / kappa[kappa > 0])
     s = g + nu * kappa

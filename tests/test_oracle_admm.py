@@ -63,19 +63,23 @@ def test_residual_zero_at_lp_certificate(ora):
     assert n > 40
 
 
-def test_one_iteration_step2_matches_dense_assembly(ora):
+@pytest.mark.parametrize("damp,rho_box", [(0.0, 0.0), (100.0, 100.0), (7.0, 30.0)])
+def test_one_iteration_step2_matches_dense_assembly(ora, damp, rho_box):
     """After one iteration, s^1 and u^1 equal the dense-KKT solution of the
     step-2 problem built here independently: linearised Euler dynamics at
-    (s^0, u^0), tracking cost of eqn:navigation_cost and the Gauss-Newton
-    penalty sigma/2 |r0 + J (s_t - s_t^0)|^2 of every pair with y^1."""
+    (s^0, u^0), tracking cost of eqn:navigation_cost, the Gauss-Newton
+    penalty sigma/2 |r0 + J (s_t - s_t^0)|^2 of every pair with y^1, the
+    proximal damping damp/2 |(s,u) - (s,u)^0|^2 and the box block's term
+    rho_box/2 |(s,u) - z + w|^2 on bounded components (z = clip((s,u)^0), w = 0)."""
     sc = synth.config1()
     m = sc.model
     sigma = 300.0
     rng = np.random.default_rng(4)
     s0 = synth.random_states(sc, rng, 0.5, 0.1)
     s0[0] = sc.s_ref[0]
-    u0 = rng.normal(0, 0.1, sc.u_init.shape)
-    out = ora.admm_batch(sc, sigma=sigma, prox=1e-3, max_iter=1, s=s0, u=u0)
+    s0[:, 3] = np.clip(s0[:, 3] + rng.normal(0, 20, len(s0)), -5, 40)   # some speeds out of the box
+    u0 = rng.normal(0, 0.3, sc.u_init.shape)
+    out = ora.admm_batch(sc, sigma=sigma, prox=1e-3, max_iter=1, s=s0, u=u0, damp=damp, rho_box=rho_box)
     N, ns, nu = int(sc.horizon[0]), m.ns, m.nu
     A = np.zeros((N, ns, ns))
     B = np.zeros((N, ns, nu))
@@ -89,6 +93,14 @@ def test_one_iteration_step2_matches_dense_assembly(ora):
     q = -2 * m.Qs[None, :] * sc.s_ref
     R = np.repeat(np.diag(2 * m.Qu)[None], N, 0)
     r = np.zeros((N, nu))
+    sb = np.isfinite(m.s_lo) | np.isfinite(m.s_hi)
+    ub = np.isfinite(m.u_lo) | np.isfinite(m.u_hi)
+    for t in range(1, N + 1):
+        Q[t] += np.diag(damp + rho_box * sb)
+        q[t] -= damp * s0[t] + rho_box * sb * np.clip(s0[t], m.s_lo, m.s_hi)
+    for t in range(N):
+        R[t] += np.diag(damp + rho_box * ub)
+        r[t] -= damp * u0[t] + rho_box * ub * np.clip(u0[t], m.u_lo, m.u_hi)
     for p in range(sc.n_pairs):
         j, pt, t, C, d = _pair_data(sc, p)
         r0, J = ora.pair_gn(m, sc.part_A[pt], C, d, sc.part_link[pt], sc.part_off[pt], s0[t],
@@ -104,8 +116,8 @@ def test_zeta_increment_identity(ora):
     """eqn:ADMM_residue_updates: zeta^{k+1} - zeta^k = T(s^{k+1}, y^{k+1}),
     xi^{k+1} - xi^k = R(s^{k+1}, y^{k+1}), and r_pri is their squared sum."""
     sc = synth.config2()
-    a = ora.admm_batch(sc, prox=1e-3, max_iter=3)
-    b = ora.admm_batch(sc, prox=1e-3, max_iter=4)
+    a = ora.admm_batch(sc, prox=1e-3, max_iter=3, rho_box=0.0)
+    b = ora.admm_batch(sc, prox=1e-3, max_iter=4, rho_box=0.0)
     sk, yk = b["s"], b["y"]
     dz = b["zeta"] - a["zeta"]
     dx = b["xi"] - a["xi"]
@@ -121,9 +133,10 @@ def test_zeta_increment_identity(ora):
 
 def test_converged_fixed_point_is_collision_free(ora):
     """At a point meeting the stopping rule, every pair's certificate is
-    (nearly) feasible, so alpha* of the final trajectory is >= 1 - O(sqrt(eps))."""
+    (nearly) feasible, so alpha* of the final trajectory is >= 1 - O(sqrt(eps)),
+    and the box block holds the controls within their bounds."""
     sc = synth.config1()
-    out = ora.admm_batch(sc, prox=1e-3, max_iter=300)
+    out = ora.admm_batch(sc, max_iter=300)
     assert out["status"][0] == 0
     assert out["r_pri"][0] <= 1e-4 and out["r_dual"][0] <= 1e-4
     al = ora.scale_batch(sc, out["s"])["alpha"]
@@ -131,6 +144,8 @@ def test_converged_fixed_point_is_collision_free(ora):
     # the reference runs through an obstacle: the plan deviates from it
     al_ref = ora.scale_batch(sc, sc.s_ref)["alpha"]
     assert al_ref.min() < 0.9
+    m = sc.model
+    assert (out["u"] >= m.u_lo - 1e-2).all() and (out["u"] <= m.u_hi + 1e-2).all()
 
 
 def test_far_obstacles_reduce_to_tracking(ora):
@@ -143,6 +158,6 @@ def test_far_obstacles_reduce_to_tracking(ora):
     rng = np.random.default_rng(0)
     s0 = synth.random_states(sc, rng, 0.3, 0.05)
     s0[0] = sc.s_ref[0]
-    out = ora.admm_batch(sc, prox=1e-3, max_iter=1000, s=s0, eps_pri=1e-14, eps_dual=1e-14)
+    out = ora.admm_batch(sc, prox=1e-3, max_iter=1000, s=s0, eps_pri=1e-14, eps_dual=1e-14, damp=0.0)
     assert np.abs(out["s"] - sc.s_ref).max() < 1e-4
     assert out["cost"][0] < 1e-8

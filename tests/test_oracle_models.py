@@ -39,9 +39,15 @@ def test_bicycle_closed_forms(ora):
     m = synth.bicycle_model()
     f = ora.dynamics(m, [1.0, 2.0, 0.0, 5.0], [0.7, 0.0])[0]
     assert np.allclose(f, [5.0, 0.0, 0.0, 0.7])
-    # yaw rate of a kinematic bicycle: v tan(delta) / L
-    f = ora.dynamics(m, [0, 0, math.pi / 2, 4.0], [0, 0.2])[0]
-    assert np.allclose(f, [0.0, 4.0, 4.0 * math.tan(0.2) / 2.7, 0.0], atol=1e-12)
+    # yaw rate of a kinematic bicycle: v * kappa with kappa = tan(steer) / L
+    kap = math.tan(0.2) / 2.7
+    f = ora.dynamics(m, [0, 0, math.pi / 2, 4.0], [0, kap])[0]
+    assert np.allclose(f, [0.0, 4.0, 4.0 * kap, 0.0], atol=1e-12)
+    # constant curvature and speed: the Euler steps stay on a circle of radius 1/kappa to O(dt^2)
+    s = np.array([0.0, 0.0, 0.0, 5.0])
+    for _ in range(200):
+        s = s + 1e-3 * ora.dynamics(m, s, [0.0, 0.25])[0]
+    assert np.hypot(s[0], s[1] - 4.0) == pytest.approx(4.0, abs=2e-3)
 
 
 def test_trailer_closed_forms(ora):
