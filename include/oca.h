@@ -1,0 +1,244 @@
+/*
+ * oca.h -- C-ABI of the GB300-native scale-based collision-avoidance library.
+ *
+ * Method: "GPU-Accelerated Optimization-Based Collision Avoidance" (Wu, Wang,
+ * Zhang, arXiv 2406.07048).  Robot parts and obstacles are H-polyhedra
+ * (Sec. III-A); a part i and an obstacle j are collision-free at step t iff
+ * the scale LP eqn:scale_opt has alpha* >= 1, which its dual
+ * eqn:scale_opt_dual turns into constraints linear in (lambda, mu)
+ * (eqn:poly_colli_free_conts).  An MPC problem over these constraints
+ * (eqn:MPC_opt_origin) is split by ADMM (Sec. IV-B) into a batch of small
+ * per-pair QPs (eqn:const_least_square), a per-scenario trajectory QP, and
+ * elementwise dual updates.
+ *
+ * Conventions for every entry point
+ *   - Plain C: no CUDA or torch types.  `stream` is a cudaStream_t passed as
+ *     void* (NULL = legacy default stream).  Every call is stream-ordered and
+ *     asynchronous unless stated otherwise; argument errors are reported
+ *     before anything is launched.
+ *   - Device arrays are caller-owned and must stay valid until the work on
+ *     `stream` has finished.  Floating arrays all have the scene's dtype
+ *     (OCA_F32 = float, OCA_F64 = double).
+ *   - Pair-indexed arrays are component-major with the pair index fastest:
+ *     element c of pair p is at [c * P + p], P = total pairs of the scene.
+ *   - Pairs of scenario s are enumerated
+ *       p = pair_begin[s] + (j * n_parts_s + part) * N_s + (t - 1)
+ *     (obstacle j slowest, step t = 1..N_s fastest); pair_begin is the CSR of
+ *     M_s * n_parts_s * N_s, available from oca_scene_info.
+ *   - y = [lambda; mu; gamma] of a pair is stored padded: lambda_k at
+ *     component k (k < fr_max), mu_m at fr_max + m (m < fo_max), gamma at
+ *     fr_max + fo_max; ny_max = fr_max + fo_max + 1.  Components beyond a
+ *     pair's own face counts are neither read nor written.
+ *   - Per-element failures (iteration caps, non-finite data) are reported
+ *     through status arrays; nothing traps on the device.
+ */
+#ifndef OCA_H
+#define OCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OCA_OK = 0,
+    OCA_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, dtype or geometry          */
+    OCA_ERR_CUDA = 2,             /* a CUDA runtime call failed                    */
+    OCA_ERR_NO_MEMORY = 3,        /* device allocation failed (scene creation)     */
+    OCA_ERR_UNSUPPORTED = 4,      /* valid request this build does not implement   */
+    OCA_ERR_CAPACITY = 5          /* a size exceeds a compiled-in maximum           */
+} oca_status;
+
+typedef enum { OCA_F32 = 0, OCA_F64 = 1 } oca_dtype;
+
+typedef enum {
+    OCA_MODEL_BICYCLE = 0, /* s = (x, y, theta, v), u = (accel, steer), dim 2          */
+    OCA_MODEL_TRAILER = 1, /* s = (x, y, theta, v, psi), u = (accel, steer), dim 2     */
+    OCA_MODEL_QUAD = 2     /* s = (p, v, roll, pitch, yaw, body rates), u = 4 rotor
+                              thrusts relative to hover, dim 3                        */
+} oca_model_kind;
+
+/* per-pair status values (status_out of oca_pair_qp_batch / oca_scale_detect_batch) */
+enum {
+    OCA_PAIR_OK = 0,
+    OCA_PAIR_ITER_CAP = 1,   /* solver hit its iteration cap; result is the last iterate */
+    OCA_PAIR_DEGENERATE = 2, /* singular working set; result is the last valid iterate   */
+    OCA_PAIR_NONFINITE = 3   /* non-finite input or iterate                               */
+};
+
+/* per-scenario status values of oca_admm_solve */
+enum {
+    OCA_SCEN_CONVERGED = 0, /* both stopping tests of Sec. IV-B met      */
+    OCA_SCEN_MAX_ITER = 1,  /* max_iter iterations without meeting them   */
+    OCA_SCEN_FAILED = 2,    /* singular or non-finite trajectory QP       */
+    OCA_SCEN_ACTIVE = 3     /* internal: still iterating                   */
+};
+
+/* Compiled-in maxima (OCA_ERR_CAPACITY beyond them). */
+#define OCA_MAX_OBS_FACES 24
+#define OCA_MAX_PART_FACES 8
+#define OCA_MAX_HORIZON 256
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct oca_ctx oca_ctx;
+
+/* Create a context bound to CUDA device `device` (makes it current).
+ * Owns nothing per-problem; scenes own their workspaces.
+ * Errors: OCA_ERR_INVALID_ARGUMENT (out == NULL, no such device), OCA_ERR_CUDA. */
+oca_status oca_create(oca_ctx **out, int device);
+
+/* Destroy a context.  Scenes created from it must be destroyed first. */
+void oca_destroy(oca_ctx *ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char *oca_status_string(oca_status st);
+
+/* ------------------------------------------------------------------------ */
+/* Scene: H-polyhedra of robot parts and obstacles (Sec. III-A, IV-A)       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t dim;     /* 2 or 3                                                    */
+    int32_t dtype;   /* oca_dtype of every floating array of this scene          */
+    int32_t n_scen;  /* S >= 1 independent scenarios                            */
+    int32_t fo_max;  /* row stride (max faces) of the obstacle arrays, <= OCA_MAX_OBS_FACES  */
+    int32_t fr_max;  /* row stride of the part arrays, <= OCA_MAX_PART_FACES    */
+    /* host metadata, read only during oca_scene_create: */
+    const int32_t *obs_begin;  /* [S+1] CSR of obstacles over scenarios         */
+    const int32_t *obs_nf;     /* [M_tot] obstacle face counts, 1..fo_max       */
+    const int32_t *part_begin; /* [S+1] CSR of robot parts over scenarios       */
+    const int32_t *part_nf;    /* [P_tot] part face counts, 1..fr_max           */
+    const int32_t *part_link;  /* [P_tot] 0 = vehicle body, 1 = trailer link    */
+    const int32_t *horizon;    /* [S] N_s, 1..OCA_MAX_HORIZON                   */
+    /* device geometry, caller-owned, must outlive the scene: */
+    const void *obs_C;    /* [M_tot][fo_max][dim] outward normals c_m (world)   */
+    const void *obs_d;    /* [M_tot][fo_max] offsets d_m:  C y <= d             */
+    const void *part_A;   /* [P_tot][fr_max][dim] body-frame normals a_k        */
+    const void *part_b;   /* [P_tot][fr_max] offsets b_k > 0 (centre inside)    */
+    const void *part_off; /* [P_tot][dim] part centre in its link frame         */
+} oca_scene_desc;
+
+typedef struct oca_scene oca_scene;
+
+typedef struct {
+    int64_t n_pairs;   /* P = sum_s M_s * n_parts_s * N_s                       */
+    int64_t n_states;  /* sum_s (N_s + 1): rows of the state arrays             */
+    int64_t n_ctrls;   /* sum_s N_s: rows of the control arrays                 */
+    int32_t ny_max;    /* fr_max + fo_max + 1                                   */
+    int32_t n_tiles;   /* work tiles of the pair kernels                        */
+    const int64_t *pair_begin; /* host [S+1], owned by the scene                */
+    const int64_t *state_begin;/* host [S+1]                                     */
+    const int64_t *ctrl_begin; /* host [S+1]                                     */
+} oca_scene_info;
+
+/* Validate a scene and allocate its device workspace (the only allocating
+ * call besides oca_create).  Reads the host metadata and checks, on the
+ * device, that part offsets are > 0 and all geometry is finite.
+ * Errors: OCA_ERR_INVALID_ARGUMENT, OCA_ERR_CAPACITY, OCA_ERR_NO_MEMORY,
+ * OCA_ERR_CUDA.  Synchronous. */
+oca_status oca_scene_create(oca_ctx *ctx, const oca_scene_desc *desc, oca_scene **out);
+void oca_scene_destroy(oca_scene *scene);
+oca_status oca_scene_info_get(const oca_scene *scene, oca_scene_info *info);
+
+/* Work shape of the pair kernels: warps per 32-lane tile (1..16); each warp
+ * sweeps every W-th obstacle of the tile's scenario.  oca_scene_create picks
+ * about eight obstacles per warp at the median obstacle count; the tuner in
+ * the Python binding times the candidates and sets the fastest.
+ * Errors: OCA_ERR_INVALID_ARGUMENT. */
+oca_status oca_scene_set_warps(oca_scene *scene, int warps);
+int oca_scene_get_warps(const oca_scene *scene); /* -1 if scene == NULL */
+
+/* ------------------------------------------------------------------------ */
+/* Model and ADMM parameters                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t kind;     /* oca_model_kind; must match the scene's dim           */
+    double dt;        /* Euler step of eqn:system_eqn: s+ = s + dt f_c(s,u)   */
+    double param[8];  /* bicycle [L]; trailer [L, M_hitch, L2]; quad
+                         [m, g, Jx, Jy, Jz, arm, yaw_coeff]                     */
+    double Qs[12];    /* diagonal of Q_s (eqn:navigation_cost)                 */
+    double Qu[4];     /* diagonal of Q_u                                        */
+    double s_lo[12], s_hi[12]; /* state box of eqn:MPC_opt_origin; +-inf (or
+                                  magnitude >= 1e30) leaves a component free    */
+    double u_lo[4], u_hi[4];   /* control box                                    */
+} oca_model;
+
+typedef struct {
+    double sigma;     /* ADMM penalty (eqn:ADMM_Lagrangian), paper: 300            */
+    double eps_pri;   /* stop when sum(dzeta^2 + |dxi|^2) <= eps_pri (Sec. IV-B)    */
+    double eps_dual;  /* and sum(|dlambda|^2 + |dmu|^2) <= eps_dual                  */
+    double prox;      /* >= 0; proximal weight 0.5*prox*sum_g |K_g|^2 (y_g - y^k_g)^2 in
+                         step 1, each generator's step measured in residual space
+                         (0 = the paper's QP as printed)                               */
+    int32_t max_iter; /* iteration cap                                                */
+    int32_t flags;    /* OCA_ADMM_* bits                                              */
+    double rho_box;   /* >= 0; penalty of the box block: the state/control boxes are
+                         a bounded copy z of (s, u) with scaled dual w, updated
+                         after each trajectory step (z = clip(s + w), w += s - z);
+                         its residuals |s - z|^2 and |dz|^2 join r_pri and r_dual  */
+    double damp;      /* >= 0; proximal weight 0.5*damp*|(s,u) - (s,u)^k|^2 in step 2 */
+} oca_admm_params;
+
+#define OCA_ADMM_RICCATI_F32 1  /* factorise the trajectory QP in FP32 (default FP64) */
+
+/* Per-scenario results, all device arrays of length S (float arrays: scene dtype). */
+typedef struct {
+    int32_t *iters;  /* iterations performed                                    */
+    int32_t *status; /* OCA_SCEN_*                                               */
+    void *r_pri;     /* primal residual sum of the last iteration                */
+    void *r_dual;    /* dual residual sum of the last iteration                  */
+    void *cost;      /* F of eqn:navigation_cost at the returned trajectory     */
+} oca_admm_report;
+
+/* ------------------------------------------------------------------------ */
+/* Hot-path entry points                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Scale-based collision detection, Sec. III-A eqn:scale_opt, per pair:
+ *   alpha* = min alpha s.t. A x <= alpha b, C' x <= d'  (body frame of the part,
+ *   C' = C R(s_t), d' = d - C rho(s_t)), solved through the dual
+ *   eqn:scale_opt_dual; alpha* >= 1 means collision-free.
+ * states : [n_states][ns] row-major (s_t of scenario s at row state_begin[s]+t).
+ * alpha  : [P] out.  lambda: [fr_max][P] out or NULL.  mu: [fo_max][P] out or NULL.
+ * margin : [P] double out or NULL: FP64 weak-duality lower bound
+ *          -d'^T mu / (b^T lambda + |A^T lambda + C'^T mu| D_R) on alpha*
+ *          (D_R = largest vertex norm of the part), Sec. III-B.
+ * verdict: [P] int32 out or NULL: 1 if alpha* >= 1 (free), else 0.
+ * status : [P] int32 out or NULL: OCA_PAIR_*. */
+oca_status oca_scale_detect_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                                  const void *states, void *alpha, void *lambda, void *mu,
+                                  double *margin, int32_t *verdict, int32_t *status, void *stream);
+
+/* ADMM step 1 alone, Sec. IV-C eqn:const_least_square, per pair:
+ *   min 0.5 |K^T y + bq|^2 + 0.5 prox sum_g |K_g|^2 (y_g - y_in,g)^2
+ *   s.t. b_i^T lambda = 1, y = [lambda; mu; gamma] >= 0,
+ * with K built at the pose of s_t and bq = [1 + zeta; xi].
+ * zeta: [P], xi: [dim][P] in.  y_in: [ny_max][P] in (warm start; also the
+ * proximal centre); y_out: [ny_max][P] out (may alias y_in).
+ * v_out: [dim+1][P] = K^T y + bq out or NULL.  obj_out: [P] = 0.5|v|^2 or NULL.
+ * status_out: [P] int32 OCA_PAIR_* or NULL. */
+oca_status oca_pair_qp_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                             const void *states, const void *zeta, const void *xi, double prox,
+                             const void *y_in, void *y_out, void *v_out, void *obj_out,
+                             int32_t *status_out, void *stream);
+
+/* Whole ADMM solves of every scenario (Sec. IV-B), Gauss-Seidel order:
+ * step 1 pair QPs, step 2 one LQ (SQP) step of the trajectory problem with
+ * linearised dynamics and Gauss-Newton-linearised pair residuals, solved by
+ * a Riccati recursion, step 3 zeta += T, xi += R; per-scenario stopping rule.
+ * s_ref: [n_states][ns] in.  s: [n_states][ns] in/out (row t=0 of each
+ * scenario is the fixed initial state).  u: [n_ctrls][nu] in/out.
+ * y: [ny_max][P] in/out (initial y^0 / result).  zeta: [P], xi: [dim][P] in/out.
+ * report: device arrays, out.  Runs to completion on `stream` (the host waits
+ * between iteration chunks to test whether every scenario has stopped). */
+oca_status oca_admm_solve(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                          const oca_admm_params *params, const void *s_ref, void *s, void *u,
+                          void *y, void *zeta, void *xi, const oca_admm_report *report,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCA_H */

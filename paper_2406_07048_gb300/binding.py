@@ -1,0 +1,293 @@
+"""Python binding of the C-ABI in include/oca.h (argument marshalling only).
+
+Device memory and streams come from PyTorch; every computation runs in
+``liboca.so``.  There is no CPU fallback: if the library is missing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboca.so")
+_lib = None
+
+OCA_OK = 0
+STATUS_NAMES = {0: "OCA_OK", 1: "OCA_ERR_INVALID_ARGUMENT", 2: "OCA_ERR_CUDA", 3: "OCA_ERR_NO_MEMORY",
+                4: "OCA_ERR_UNSUPPORTED", 5: "OCA_ERR_CAPACITY"}
+OCA_ADMM_RICCATI_F32 = 1
+MAX_OBS_FACES, MAX_PART_FACES, MAX_HORIZON = 24, 8, 256
+
+
+class OcaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("dtype", C.c_int32), ("n_scen", C.c_int32), ("fo_max", C.c_int32),
+                ("fr_max", C.c_int32), ("obs_begin", C.c_void_p), ("obs_nf", C.c_void_p),
+                ("part_begin", C.c_void_p), ("part_nf", C.c_void_p), ("part_link", C.c_void_p),
+                ("horizon", C.c_void_p), ("obs_C", C.c_void_p), ("obs_d", C.c_void_p), ("part_A", C.c_void_p),
+                ("part_b", C.c_void_p), ("part_off", C.c_void_p)]
+
+
+class SceneInfo(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("n_states", C.c_int64), ("n_ctrls", C.c_int64), ("ny_max", C.c_int32),
+                ("n_tiles", C.c_int32), ("pair_begin", C.POINTER(C.c_int64)),
+                ("state_begin", C.POINTER(C.c_int64)), ("ctrl_begin", C.POINTER(C.c_int64))]
+
+
+class ModelC(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dt", C.c_double), ("param", C.c_double * 8), ("Qs", C.c_double * 12),
+                ("Qu", C.c_double * 4), ("s_lo", C.c_double * 12), ("s_hi", C.c_double * 12),
+                ("u_lo", C.c_double * 4), ("u_hi", C.c_double * 4)]
+
+
+class AdmmParams(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("eps_pri", C.c_double), ("eps_dual", C.c_double), ("prox", C.c_double),
+                ("max_iter", C.c_int32), ("flags", C.c_int32), ("rho_box", C.c_double), ("damp", C.c_double)]
+
+
+class Report(C.Structure):
+    _fields_ = [("iters", C.c_void_p), ("status", C.c_void_p), ("r_pri", C.c_void_p), ("r_dual", C.c_void_p),
+                ("cost", C.c_void_p)]
+
+
+EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create", "oca_scene_destroy",
+            "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
+            "oca_pair_qp_batch", "oca_admm_solve"]
+
+
+def lib():
+    """Load liboca.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I, D = C.c_void_p, C.c_int, C.c_double
+        L.oca_create.argtypes = [C.POINTER(P), I]
+        L.oca_create.restype = I
+        L.oca_destroy.argtypes = [P]
+        L.oca_destroy.restype = None
+        L.oca_status_string.argtypes = [I]
+        L.oca_status_string.restype = C.c_char_p
+        L.oca_scene_create.argtypes = [P, C.POINTER(SceneDesc), C.POINTER(P)]
+        L.oca_scene_create.restype = I
+        L.oca_scene_destroy.argtypes = [P]
+        L.oca_scene_destroy.restype = None
+        L.oca_scene_info_get.argtypes = [P, C.POINTER(SceneInfo)]
+        L.oca_scene_info_get.restype = I
+        L.oca_scene_set_warps.argtypes = [P, I]
+        L.oca_scene_set_warps.restype = I
+        L.oca_scene_get_warps.argtypes = [P]
+        L.oca_scene_get_warps.restype = I
+        L.oca_scale_detect_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, P, P, P, P, P]
+        L.oca_scale_detect_batch.restype = I
+        L.oca_pair_qp_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, D, P, P, P, P, P, P]
+        L.oca_pair_qp_batch.restype = I
+        L.oca_admm_solve.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, P, P, P, P,
+                                     C.POINTER(Report), P]
+        L.oca_admm_solve.restype = I
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != OCA_OK:
+        raise OcaError(code, where)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def model_c(m: synth.Model) -> ModelC:
+    mc = ModelC()
+    mc.kind = int(m.kind)
+    mc.dt = float(m.dt)
+    for i, v in enumerate(m.param):
+        mc.param[i] = float(v)
+    for i, v in enumerate(m.Qs):
+        mc.Qs[i] = float(v)
+    for i, v in enumerate(m.Qu):
+        mc.Qu[i] = float(v)
+    for i in range(12):
+        mc.s_lo[i], mc.s_hi[i] = -float("inf"), float("inf")
+    for i in range(4):
+        mc.u_lo[i], mc.u_hi[i] = -float("inf"), float("inf")
+    for name in ("s_lo", "s_hi", "u_lo", "u_hi"):
+        arr = getattr(m, name, None)
+        if arr is not None:
+            for i, v in enumerate(arr):
+                getattr(mc, name)[i] = float(v)
+    return mc
+
+
+class Context:
+    """oca_create / oca_destroy."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = C.c_void_p()
+        _check(lib().oca_create(C.byref(h), int(device)), "oca_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().oca_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceScene:
+    """A synthetic scene uploaded to the GPU and prepared by oca_scene_create."""
+
+    def __init__(self, ctx: Context, scene: synth.Scene, dtype=torch.float32):
+        self.ctx, self.scene, self.dtype = ctx, scene, dtype
+        dev = torch.device("cuda", ctx.device)
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=dev).contiguous()
+        self.obs_C, self.obs_d = f(scene.obs_C), f(scene.obs_d)
+        self.part_A, self.part_b, self.part_off = f(scene.part_A), f(scene.part_b), f(scene.part_off)
+        i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+        self._host = [i32(scene.obs_begin), i32(scene.obs_nf), i32(scene.part_begin), i32(scene.part_nf),
+                      i32(scene.part_link), i32(scene.horizon)]
+        d = SceneDesc()
+        d.dim, d.dtype, d.n_scen = scene.dim, 1 if dtype == torch.float64 else 0, scene.n_scen
+        d.fo_max, d.fr_max = scene.fo_max, scene.fr_max
+        d.obs_begin, d.obs_nf, d.part_begin, d.part_nf, d.part_link, d.horizon = [a.ctypes.data for a in self._host]
+        d.obs_C, d.obs_d = self.obs_C.data_ptr(), self.obs_d.data_ptr()
+        d.part_A, d.part_b, d.part_off = self.part_A.data_ptr(), self.part_b.data_ptr(), self.part_off.data_ptr()
+        self.desc = d
+        h = C.c_void_p()
+        _check(lib().oca_scene_create(ctx.h, C.byref(d), C.byref(h)), "oca_scene_create")
+        self.h = h
+        info = SceneInfo()
+        _check(lib().oca_scene_info_get(h, C.byref(info)), "oca_scene_info_get")
+        self.n_pairs, self.n_states, self.n_ctrls = info.n_pairs, info.n_states, info.n_ctrls
+        self.ny_max, self.n_tiles = info.ny_max, info.n_tiles
+        assert self.n_pairs == scene.n_pairs and self.ny_max == scene.ny_max
+        self.model = model_c(scene.model)
+        self.device = dev
+
+    @property
+    def warps(self) -> int:
+        return int(lib().oca_scene_get_warps(self.h))
+
+    @warps.setter
+    def warps(self, w: int):
+        _check(lib().oca_scene_set_warps(self.h, int(w)), "oca_scene_set_warps")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().oca_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- helpers for pair-indexed arrays ----------------------------------
+    def tensor(self, a, dtype=None) -> torch.Tensor:
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or self.dtype, device=self.device).contiguous()
+
+    def to_device_pairs(self, pair_major: np.ndarray) -> torch.Tensor:
+        """[P, k] pair-major host array -> [k, P] component-major device tensor."""
+        return self.tensor(np.ascontiguousarray(np.asarray(pair_major).reshape(self.n_pairs, -1).T))
+
+    @staticmethod
+    def to_host_pairs(comp_major: torch.Tensor) -> np.ndarray:
+        """[k, P] component-major device tensor -> [P, k] pair-major float64 array."""
+        return comp_major.double().cpu().numpy().T.copy()
+
+
+def scale_detect(ds: DeviceScene, states: torch.Tensor, want_certificate: bool = True, want_margin: bool = True,
+                 stream=None):
+    """oca_scale_detect_batch: alpha*, lambda*, mu*, FP64 margin, verdict, status."""
+    P = ds.n_pairs
+    alpha = torch.empty(P, dtype=ds.dtype, device=ds.device)
+    lam = torch.zeros(ds.scene.fr_max, P, dtype=ds.dtype, device=ds.device) if want_certificate else None
+    mu = torch.zeros(ds.scene.fo_max, P, dtype=ds.dtype, device=ds.device) if want_certificate else None
+    margin = torch.empty(P, dtype=torch.float64, device=ds.device) if want_margin else None
+    verdict = torch.empty(P, dtype=torch.int32, device=ds.device)
+    status = torch.empty(P, dtype=torch.int32, device=ds.device)
+    _check(lib().oca_scale_detect_batch(ds.ctx.h, ds.h, C.byref(ds.model), _ptr(states), _ptr(alpha), _ptr(lam),
+                                        _ptr(mu), _ptr(margin), _ptr(verdict), _ptr(status), _stream(stream)),
+           "oca_scale_detect_batch")
+    return dict(alpha=alpha, lam=lam, mu=mu, margin=margin, verdict=verdict, status=status)
+
+
+def pair_qp(ds: DeviceScene, states, zeta, xi, y_in, prox: float = 0.0, y_out=None, want_v=True, stream=None):
+    """oca_pair_qp_batch: y_out, v = K^T y + bq, obj, status."""
+    P = ds.n_pairs
+    if y_out is None:
+        y_out = torch.zeros_like(y_in)
+    v = torch.empty(ds.scene.dim + 1, P, dtype=ds.dtype, device=ds.device) if want_v else None
+    obj = torch.empty(P, dtype=ds.dtype, device=ds.device) if want_v else None
+    status = torch.empty(P, dtype=torch.int32, device=ds.device)
+    _check(lib().oca_pair_qp_batch(ds.ctx.h, ds.h, C.byref(ds.model), _ptr(states), _ptr(zeta), _ptr(xi),
+                                   float(prox), _ptr(y_in), _ptr(y_out), _ptr(v), _ptr(obj), _ptr(status),
+                                   _stream(stream)), "oca_pair_qp_batch")
+    return dict(y=y_out, v=v, obj=obj, status=status)
+
+
+DEFAULTS = dict(sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1e-2, max_iter=300, rho_box=100.0, damp=100.0)
+
+
+def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1e-2,
+               max_iter=300, flags=0, rho_box=100.0, damp=100.0, stream=None):
+    """oca_admm_solve: updates s, u, y, zeta, xi in place; returns the report."""
+    S = ds.scene.n_scen
+    rep_t = dict(iters=torch.zeros(S, dtype=torch.int32, device=ds.device),
+                 status=torch.full((S,), -1, dtype=torch.int32, device=ds.device),
+                 r_pri=torch.zeros(S, dtype=ds.dtype, device=ds.device),
+                 r_dual=torch.zeros(S, dtype=ds.dtype, device=ds.device),
+                 cost=torch.zeros(S, dtype=ds.dtype, device=ds.device))
+    rep = Report(rep_t["iters"].data_ptr(), rep_t["status"].data_ptr(), rep_t["r_pri"].data_ptr(),
+                 rep_t["r_dual"].data_ptr(), rep_t["cost"].data_ptr())
+    pr = AdmmParams(float(sigma), float(eps_pri), float(eps_dual), float(prox), int(max_iter), int(flags),
+                    float(rho_box), float(damp))
+    _check(lib().oca_admm_solve(ds.ctx.h, ds.h, C.byref(ds.model), C.byref(pr), _ptr(s_ref), _ptr(s), _ptr(u),
+                                _ptr(y), _ptr(zeta), _ptr(xi), C.byref(rep), _stream(stream)), "oca_admm_solve")
+    return rep_t
+
+
+class Problem:
+    """Device-resident ADMM state of a synthetic scene (initial guess, cold y)."""
+
+    def __init__(self, ds: DeviceScene, s_init=None, u_init=None, y_init=None):
+        sc = ds.scene
+        self.ds = ds
+        self.s_ref = ds.tensor(sc.s_ref)
+        self.s = ds.tensor(sc.s_init if s_init is None else s_init)
+        self.u = ds.tensor(sc.u_init if u_init is None else u_init)
+        self.y = ds.to_device_pairs(sc.cold_y() if y_init is None else y_init)
+        self.zeta = torch.zeros(ds.n_pairs, dtype=ds.dtype, device=ds.device)
+        self.xi = torch.zeros(sc.dim, ds.n_pairs, dtype=ds.dtype, device=ds.device)
+
+    def solve(self, **kw):
+        return admm_solve(self.ds, self.s_ref, self.s, self.u, self.y, self.zeta, self.xi, **kw)

@@ -1,0 +1,733 @@
+// Host side of the C-ABI declared in include/oca.h: argument checking, scene
+// preparation (metadata, work tiles, workspace), kernel orchestration and the
+// ADMM iteration driver (CUDA-graph chunks of iterations, per-scenario
+// retirement on the device, host check between chunks).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "oca_common.cuh"
+#include "oca_kernels.h"
+
+using namespace oca;
+
+struct oca_ctx {
+    int device;
+    int n_sm;
+};
+
+struct oca_scene {
+    oca_ctx *ctx = nullptr;
+    int dim = 0, dtype = 0, S = 0, FO = 0, FR = 0, M_tot = 0, P_tot = 0;
+    std::vector<ScenMeta> meta;
+    std::vector<int64_t> pair_begin, state_begin, ctrl_begin;
+    int64_t P = 0, n_states = 0, n_ctrls = 0;
+    int Qtot = 0, maxQ = 0, n_tiles = 0, ny_max = 0, W = 1, maxN = 0;
+    const void *obs_C = nullptr, *obs_d = nullptr, *part_A = nullptr, *part_b = nullptr, *part_off = nullptr;
+    // device
+    ScenMeta *d_meta = nullptr;
+    Tile *d_tiles = nullptr;
+    int *d_obs_nf = nullptr, *d_part_nf = nullptr, *d_part_link = nullptr;
+    double *d_part_radius = nullptr;
+    void *d_pose = nullptr, *d_stats = nullptr, *d_y2 = nullptr, *d_ric = nullptr;
+    double *d_res = nullptr;
+    long long *d_ric_off = nullptr;
+    int *d_status = nullptr, *d_iter = nullptr, *d_active = nullptr, *d_err = nullptr;
+    void *d_box = nullptr;      // z_s, w_s [n_states][NSmax]; z_u, w_u [n_ctrls][NUmax]
+    double *d_box_res = nullptr;  // [S][2]
+    int ns_max = 0, nu_max = 0;
+    int *h_active = nullptr;
+};
+
+namespace {
+
+#define OCA_CK(x)                                  \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return OCA_ERR_CUDA; \
+    } while (0)
+
+size_t dsize(int dtype) { return dtype == OCA_F64 ? sizeof(double) : sizeof(float); }
+
+template <typename T>
+Geom<T> make_geom(const oca_scene *sc) {
+    Geom<T> g;
+    g.obs_C = static_cast<const T *>(sc->obs_C);
+    g.obs_d = static_cast<const T *>(sc->obs_d);
+    g.obs_nf = sc->d_obs_nf;
+    g.part_A = static_cast<const T *>(sc->part_A);
+    g.part_b = static_cast<const T *>(sc->part_b);
+    g.part_nf = sc->d_part_nf;
+    g.part_link = sc->d_part_link;
+    g.part_off = static_cast<const T *>(sc->part_off);
+    g.FO = sc->FO;
+    g.FR = sc->FR;
+    return g;
+}
+
+template <typename T>
+DevModel<T> make_model(const oca_model *m) {
+    DevModel<T> d;
+    d.kind = m->kind;
+    d.dt = T(m->dt);
+    for (int i = 0; i < 8; ++i) d.p[i] = T(m->param[i]);
+    for (int i = 0; i < 12; ++i) d.Qs[i] = T(m->Qs[i]);
+    for (int i = 0; i < 4; ++i) d.Qu[i] = T(m->Qu[i]);
+    auto cl = [](double v) { return T(v < -1e30 ? -1e30 : (v > 1e30 ? 1e30 : v)); };
+    for (int i = 0; i < 12; ++i) {
+        d.s_lo[i] = cl(m->s_lo[i]);
+        d.s_hi[i] = cl(m->s_hi[i]);
+    }
+    for (int i = 0; i < 4; ++i) {
+        d.u_lo[i] = cl(m->u_lo[i]);
+        d.u_hi[i] = cl(m->u_hi[i]);
+    }
+    return d;
+}
+
+int model_ns(int kind) { return kind == 0 ? 4 : kind == 1 ? 5 : 12; }
+
+oca_status check_model(const oca_scene *sc, const oca_model *m) {
+    if (!m || m->kind < 0 || m->kind > 2) return OCA_ERR_INVALID_ARGUMENT;
+    if ((m->kind == 2) != (sc->dim == 3)) return OCA_ERR_INVALID_ARGUMENT;
+    if (!(m->dt > 0.0) || !std::isfinite(m->dt)) return OCA_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < 12; ++i)
+        if (std::isnan(m->s_lo[i]) || std::isnan(m->s_hi[i]) || m->s_lo[i] > m->s_hi[i]) return OCA_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < 4; ++i)
+        if (std::isnan(m->u_lo[i]) || std::isnan(m->u_hi[i]) || m->u_lo[i] > m->u_hi[i]) return OCA_ERR_INVALID_ARGUMENT;
+    return OCA_OK;
+}
+
+// ---- scene validation: part offsets positive, geometry finite; radius of
+// each part (largest vertex norm, by enumerating dim-subsets of faces) for the
+// certificate margin.
+template <typename T>
+__global__ void k_validate(const T *obs_C, const T *obs_d, const int *obs_nf, int M_tot, const T *part_A,
+                           const T *part_b, const int *part_nf, int P_tot, const T *part_off, int FO, int FR,
+                           int dim, double *radius, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M_tot) {
+        const int nf = obs_nf[i];
+        for (int k = 0; k < nf * dim; ++k)
+            if (!isfinite(double(obs_C[(long long)i * FO * dim + k]))) atomicOr(err, 1);
+        for (int k = 0; k < nf; ++k)
+            if (!isfinite(double(obs_d[(long long)i * FO + k]))) atomicOr(err, 1);
+    }
+    if (i < P_tot) {
+        const int nr = part_nf[i];
+        const T *A = part_A + (long long)i * FR * dim;
+        const T *b = part_b + (long long)i * FR;
+        for (int k = 0; k < nr; ++k) {
+            if (!(double(b[k]) > 0.0) || !isfinite(double(b[k]))) atomicOr(err, 2);
+            for (int l = 0; l < dim; ++l)
+                if (!isfinite(double(A[k * dim + l]))) atomicOr(err, 2);
+        }
+        for (int l = 0; l < dim; ++l)
+            if (!isfinite(double(part_off[(long long)i * dim + l]))) atomicOr(err, 2);
+        double rmax = 0.0;
+        int nv = 0;
+        for (int a = 0; a < nr; ++a)
+            for (int b2 = a + 1; b2 < nr; ++b2)
+                for (int c = (dim == 3 ? b2 + 1 : 0); c < (dim == 3 ? nr : 1); ++c) {
+                    double x[3];
+                    if (dim == 2) {
+                        const double a00 = A[a * 2], a01 = A[a * 2 + 1], a10 = A[b2 * 2], a11 = A[b2 * 2 + 1];
+                        const double det = a00 * a11 - a01 * a10;
+                        if (fabs(det) < 1e-12) continue;
+                        x[0] = (double(b[a]) * a11 - a01 * double(b[b2])) / det;
+                        x[1] = (a00 * double(b[b2]) - double(b[a]) * a10) / det;
+                    } else {
+                        double M[3][3], r[3];
+                        const int id[3] = {a, b2, c};
+                        for (int u = 0; u < 3; ++u) {
+                            for (int v = 0; v < 3; ++v) M[u][v] = A[id[u] * 3 + v];
+                            r[u] = b[id[u]];
+                        }
+                        const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                                           M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                                           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+                        if (fabs(det) < 1e-12) continue;
+                        for (int col = 0; col < 3; ++col) {
+                            double Mc[3][3];
+                            for (int u = 0; u < 3; ++u)
+                                for (int v = 0; v < 3; ++v) Mc[u][v] = (v == col) ? r[u] : M[u][v];
+                            x[col] = (Mc[0][0] * (Mc[1][1] * Mc[2][2] - Mc[1][2] * Mc[2][1]) -
+                                      Mc[0][1] * (Mc[1][0] * Mc[2][2] - Mc[1][2] * Mc[2][0]) +
+                                      Mc[0][2] * (Mc[1][0] * Mc[2][1] - Mc[1][1] * Mc[2][0])) / det;
+                        }
+                    }
+                    bool feas = true;
+                    for (int k = 0; k < nr && feas; ++k) {
+                        double sacc = 0.0;
+                        for (int l = 0; l < dim; ++l) sacc += double(A[k * dim + l]) * x[l];
+                        if (sacc > double(b[k]) + 1e-9 * (1.0 + fabs(double(b[k])))) feas = false;
+                    }
+                    if (!feas) continue;
+                    double n2 = 0.0;
+                    for (int l = 0; l < dim; ++l) n2 += x[l] * x[l];
+                    rmax = fmax(rmax, sqrt(n2));
+                    ++nv;
+                }
+        if (nv < dim + 1) atomicOr(err, 4);  // unbounded or degenerate part
+        radius[i] = rmax;
+    }
+}
+
+__global__ void k_reset(int *status, int S, int *iter, int *active) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S) status[i] = kActive;
+    if (i == 0) {
+        *iter = 0;
+        *active = S;
+    }
+}
+
+__global__ void k_advance(int *iter) { *iter += 1; }
+
+// box block initial state: z = clip(s or u), w = 0 (bounds passed by value)
+template <typename T>
+struct Bounds12 {
+    T lo[12], hi[12];
+};
+
+template <typename T>
+__global__ void k_box_init(const T *x, long long n, int nc, Bounds12<T> b, T *z, T *w) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nc) return;
+    const int c = (int)(i % nc);
+    z[i] = fmin(fmax(x[i], b.lo[c]), b.hi[c]);
+    w[i] = T(0);
+}
+
+// final y of a scenario retired at iteration j lives in buffer j % 2
+template <typename T>
+__global__ void k_gather(const ScenMeta *meta, const int *iters, const T *y2, T *y, long long P, int ny) {
+    const int s = blockIdx.y;
+    if (!(iters[s] & 1)) return;
+    const ScenMeta sm = meta[s];
+    const long long np = (long long)sm.M * sm.NP * sm.N;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np * ny; k += (long long)gridDim.x * blockDim.x) {
+        const long long c = k / np, p = sm.pair0 + k % np;
+        y[c * P + p] = y2[c * P + p];
+    }
+}
+
+template <typename T>
+oca_status scale_impl(oca_scene *sc, const oca_model *m, const void *states, void *alpha, void *lambda, void *mu,
+                      double *margin, int32_t *verdict, int32_t *status, cudaStream_t st) {
+    PoseArgs<T> pa;
+    pa.meta = sc->d_meta;
+    pa.n_scen = sc->S;
+    pa.g = make_geom<T>(sc);
+    pa.model = make_model<T>(m);
+    pa.states = static_cast<const T *>(states);
+    pa.pose = static_cast<T *>(sc->d_pose);
+    pa.Qtot = sc->Qtot;
+    pa.scen_status = nullptr;
+    OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
+    ScaleArgs<T> a;
+    a.meta = sc->d_meta;
+    a.tiles = sc->d_tiles;
+    a.g = make_geom<T>(sc);
+    a.pose = static_cast<const T *>(sc->d_pose);
+    a.Qtot = sc->Qtot;
+    a.P = sc->P;
+    a.part_radius = sc->d_part_radius;
+    a.alpha = static_cast<T *>(alpha);
+    a.lambda = static_cast<T *>(lambda);
+    a.mu = static_cast<T *>(mu);
+    a.margin = margin;
+    a.verdict = verdict;
+    a.status = status;
+    OCA_CK(launch_scale<T>(a, sc->dim, sc->n_tiles, sc->W, st));
+    return OCA_OK;
+}
+
+template <typename T>
+PairArgs<T> pair_args(oca_scene *sc) {
+    PairArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.meta = sc->d_meta;
+    a.tiles = sc->d_tiles;
+    a.g = make_geom<T>(sc);
+    a.pose = static_cast<const T *>(sc->d_pose);
+    a.Qtot = sc->Qtot;
+    a.P = sc->P;
+    a.res = sc->d_res;
+    a.n_tiles = sc->n_tiles;
+    a.stats = static_cast<T *>(sc->d_stats);
+    return a;
+}
+
+template <typename T>
+oca_status pairqp_impl(oca_scene *sc, const oca_model *m, const void *states, const void *zeta, const void *xi,
+                       double prox, const void *y_in, void *y_out, void *v_out, void *obj_out, int32_t *status_out,
+                       cudaStream_t st) {
+    PoseArgs<T> pa;
+    pa.meta = sc->d_meta;
+    pa.n_scen = sc->S;
+    pa.g = make_geom<T>(sc);
+    pa.model = make_model<T>(m);
+    pa.states = static_cast<const T *>(states);
+    pa.pose = static_cast<T *>(sc->d_pose);
+    pa.Qtot = sc->Qtot;
+    pa.scen_status = nullptr;
+    OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
+    PairArgs<T> a = pair_args<T>(sc);
+    a.zeta = const_cast<T *>(static_cast<const T *>(zeta));
+    a.xi = const_cast<T *>(static_cast<const T *>(xi));
+    a.y_in = static_cast<const T *>(y_in);
+    a.y_out = static_cast<T *>(y_out);
+    a.v_out = static_cast<T *>(v_out);
+    a.obj_out = static_cast<T *>(obj_out);
+    a.status_out = status_out;
+    a.prox = T(prox);
+    OCA_CK(launch_pair<T>(a, sc->dim, 0, prox > 0.0 ? 1 : 0, sc->n_tiles, sc->W, st));
+    return OCA_OK;
+}
+
+template <typename T>
+oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *s,
+                     void *u, void *y, void *zeta, void *xi, const oca_admm_report *rep, cudaStream_t st) {
+    k_reset<<<(sc->S + 255) / 256, 256, 0, st>>>(sc->d_status, sc->S, sc->d_iter, sc->d_active);
+    OCA_CK(cudaGetLastError());
+    const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
+    T *box = static_cast<T *>(sc->d_box);
+    T *zs = box, *ws = zs + (size_t)sc->n_states * sc->ns_max;
+    T *zu = ws + (size_t)sc->n_states * sc->ns_max, *wu = zu + (size_t)sc->n_ctrls * sc->nu_max;
+    {
+        const DevModel<T> dm = make_model<T>(m);
+        Bounds12<T> bs, bu;
+        for (int i = 0; i < 12; ++i) {
+            bs.lo[i] = dm.s_lo[i];
+            bs.hi[i] = dm.s_hi[i];
+            bu.lo[i] = i < 4 ? dm.u_lo[i] : T(0);
+            bu.hi[i] = i < 4 ? dm.u_hi[i] : T(0);
+        }
+        const long long n1 = sc->n_states * NS, n2 = sc->n_ctrls * NU;
+        k_box_init<T><<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(static_cast<const T *>(s), sc->n_states, NS, bs, zs, ws);
+        k_box_init<T><<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(static_cast<const T *>(u), sc->n_ctrls, NU, bu, zu, wu);
+        OCA_CK(cudaGetLastError());
+        OCA_CK(cudaMemsetAsync(sc->d_box_res, 0, sizeof(double) * 2 * sc->S, st));
+    }
+    PoseArgs<T> pa;
+    pa.meta = sc->d_meta;
+    pa.n_scen = sc->S;
+    pa.g = make_geom<T>(sc);
+    pa.model = make_model<T>(m);
+    pa.states = static_cast<const T *>(s);
+    pa.pose = static_cast<T *>(sc->d_pose);
+    pa.Qtot = sc->Qtot;
+    pa.scen_status = nullptr;
+    OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
+
+    PairArgs<T> a = pair_args<T>(sc);
+    a.zeta = static_cast<T *>(zeta);
+    a.xi = static_cast<T *>(xi);
+    a.y_in = static_cast<const T *>(y);
+    a.y_out = static_cast<T *>(sc->d_y2);
+    a.scen_status = sc->d_status;
+    a.iter = sc->d_iter;
+    a.max_iter = pr->max_iter;
+    a.prox = T(pr->prox);
+    const int solver = pr->prox > 0.0 ? 1 : 0;
+
+    RicArgs<T> r;
+    r.meta = sc->d_meta;
+    r.n_scen = sc->S;
+    r.g = make_geom<T>(sc);
+    r.model = make_model<T>(m);
+    r.sigma = T(pr->sigma);
+    r.eps_pri = T(pr->eps_pri);
+    r.eps_dual = T(pr->eps_dual);
+    r.rho_box = T(pr->rho_box);
+    r.damp = T(pr->damp);
+    r.box_zs = zs;
+    r.box_ws = ws;
+    r.box_zu = zu;
+    r.box_wu = wu;
+    r.box_res = sc->d_box_res;
+    r.max_iter = pr->max_iter;
+    r.iter = sc->d_iter;
+    r.s_ref = static_cast<const T *>(s_ref);
+    r.s = static_cast<T *>(s);
+    r.u = static_cast<T *>(u);
+    r.pose = static_cast<T *>(sc->d_pose);
+    r.stats = static_cast<const T *>(sc->d_stats);
+    r.Qtot = sc->Qtot;
+    r.res = sc->d_res;
+    r.n_tiles = sc->n_tiles;
+    r.scen_status = sc->d_status;
+    r.iters_out = rep->iters;
+    r.status_out = rep->status;
+    r.r_pri_out = static_cast<T *>(rep->r_pri);
+    r.r_dual_out = static_cast<T *>(rep->r_dual);
+    r.cost_out = static_cast<T *>(rep->cost);
+    r.active_count = sc->d_active;
+    r.scratch = sc->d_ric;
+    r.scratch0 = sc->d_ric_off;
+    const bool f32 = (pr->flags & OCA_ADMM_RICCATI_F32) != 0 && sizeof(T) == sizeof(float);
+
+    auto one_iter = [&]() -> cudaError_t {
+        cudaError_t e = launch_pair<T>(a, sc->dim, 1, solver, sc->n_tiles, sc->W, st);
+        if (e != cudaSuccess) return e;
+        e = launch_riccati<T>(r, f32, st);
+        if (e != cudaSuccess) return e;
+        k_advance<<<1, 1, 0, st>>>(sc->d_iter);
+        return cudaGetLastError();
+    };
+    const int G = 8;  // iterations per chunk between host checks
+    const long long n_launch = (long long)pr->max_iter + 1;  // j = 0..max_iter
+    cudaGraphExec_t exec = nullptr;
+    if (st != nullptr && n_launch > G) {
+        cudaGraph_t graph = nullptr;
+        OCA_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = one_iter();
+        cudaError_t ee = cudaStreamEndCapture(st, &graph);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return OCA_ERR_CUDA;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return OCA_ERR_CUDA;
+    }
+    oca_status out = OCA_OK;
+    for (long long done = 0; done < n_launch; done += G) {
+        if (exec) {
+            if (cudaGraphLaunch(exec, st) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
+        } else {
+            for (int k = 0; k < G && done + k < n_launch; ++k)
+                if (one_iter() != cudaSuccess) { out = OCA_ERR_CUDA; break; }
+            if (out != OCA_OK) break;
+        }
+        if (cudaMemcpyAsync(sc->h_active, sc->d_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            out = OCA_ERR_CUDA;
+            break;
+        }
+        if (*sc->h_active <= 0) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (out != OCA_OK) return out;
+    dim3 gg(64, sc->S);
+    k_gather<T><<<gg, 256, 0, st>>>(sc->d_meta, rep->iters, static_cast<const T *>(sc->d_y2), static_cast<T *>(y), sc->P,
+                                    sc->ny_max);
+    OCA_CK(cudaGetLastError());
+    return OCA_OK;
+}
+
+void free_scene(oca_scene *sc) {
+    if (!sc) return;
+    cudaFree(sc->d_meta);
+    cudaFree(sc->d_tiles);
+    cudaFree(sc->d_obs_nf);
+    cudaFree(sc->d_part_nf);
+    cudaFree(sc->d_part_link);
+    cudaFree(sc->d_part_radius);
+    cudaFree(sc->d_pose);
+    cudaFree(sc->d_stats);
+    cudaFree(sc->d_y2);
+    cudaFree(sc->d_ric);
+    cudaFree(sc->d_res);
+    cudaFree(sc->d_ric_off);
+    cudaFree(sc->d_status);
+    cudaFree(sc->d_iter);
+    cudaFree(sc->d_active);
+    cudaFree(sc->d_err);
+    cudaFree(sc->d_box);
+    cudaFree(sc->d_box_res);
+    if (sc->h_active) cudaFreeHost(sc->h_active);
+    delete sc;
+}
+
+template <typename P>
+oca_status dmalloc(P **p, size_t bytes) {
+    if (cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16) != cudaSuccess) return OCA_ERR_NO_MEMORY;
+    return OCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *oca_status_string(oca_status st) {
+    switch (st) {
+        case OCA_OK: return "OCA_OK";
+        case OCA_ERR_INVALID_ARGUMENT: return "OCA_ERR_INVALID_ARGUMENT";
+        case OCA_ERR_CUDA: return "OCA_ERR_CUDA";
+        case OCA_ERR_NO_MEMORY: return "OCA_ERR_NO_MEMORY";
+        case OCA_ERR_UNSUPPORTED: return "OCA_ERR_UNSUPPORTED";
+        case OCA_ERR_CAPACITY: return "OCA_ERR_CAPACITY";
+    }
+    return "OCA_ERR_UNKNOWN";
+}
+
+oca_status oca_create(oca_ctx **out, int device) {
+    if (!out) return OCA_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) return OCA_ERR_CUDA;
+    if (device < 0 || device >= n) return OCA_ERR_INVALID_ARGUMENT;
+    if (cudaSetDevice(device) != cudaSuccess) return OCA_ERR_CUDA;
+    oca_ctx *c = new (std::nothrow) oca_ctx;
+    if (!c) return OCA_ERR_NO_MEMORY;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return OCA_ERR_CUDA;
+    }
+    *out = c;
+    return OCA_OK;
+}
+
+void oca_destroy(oca_ctx *ctx) { delete ctx; }
+
+oca_status oca_scene_create(oca_ctx *ctx, const oca_scene_desc *d, oca_scene **out) {
+    if (!ctx || !d || !out) return OCA_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (d->dim != 2 && d->dim != 3) return OCA_ERR_INVALID_ARGUMENT;
+    if (d->dtype != OCA_F32 && d->dtype != OCA_F64) return OCA_ERR_INVALID_ARGUMENT;
+    if (d->n_scen < 1 || d->n_scen > 65535) return d->n_scen < 1 ? OCA_ERR_INVALID_ARGUMENT : OCA_ERR_CAPACITY;
+    if (d->fo_max < 1 || d->fr_max < 1) return OCA_ERR_INVALID_ARGUMENT;
+    if (d->fo_max > OCA_MAX_OBS_FACES || d->fr_max > OCA_MAX_PART_FACES) return OCA_ERR_CAPACITY;
+    if (!d->obs_begin || !d->obs_nf || !d->part_begin || !d->part_nf || !d->part_link || !d->horizon)
+        return OCA_ERR_INVALID_ARGUMENT;
+    if (!d->obs_C || !d->obs_d || !d->part_A || !d->part_b || !d->part_off) return OCA_ERR_INVALID_ARGUMENT;
+    const int S = d->n_scen;
+    if (d->obs_begin[0] != 0 || d->part_begin[0] != 0) return OCA_ERR_INVALID_ARGUMENT;
+    for (int s = 0; s < S; ++s) {
+        if (d->obs_begin[s + 1] < d->obs_begin[s] + 1) return OCA_ERR_INVALID_ARGUMENT;  // >= 1 obstacle
+        if (d->part_begin[s + 1] < d->part_begin[s] + 1) return OCA_ERR_INVALID_ARGUMENT; // >= 1 part
+        if (d->horizon[s] < 1) return OCA_ERR_INVALID_ARGUMENT;
+        if (d->horizon[s] > OCA_MAX_HORIZON) return OCA_ERR_CAPACITY;
+    }
+    const int M_tot = d->obs_begin[S], P_tot = d->part_begin[S];
+    for (int i = 0; i < M_tot; ++i)
+        if (d->obs_nf[i] < 1 || d->obs_nf[i] > d->fo_max) return OCA_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < P_tot; ++i) {
+        if (d->part_nf[i] < d->dim + 1 || d->part_nf[i] > d->fr_max) return OCA_ERR_INVALID_ARGUMENT;
+        if (d->part_link[i] < 0 || d->part_link[i] > 1 || (d->dim == 3 && d->part_link[i] != 0))
+            return OCA_ERR_INVALID_ARGUMENT;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return OCA_ERR_CUDA;
+    oca_scene *sc = new (std::nothrow) oca_scene;
+    if (!sc) return OCA_ERR_NO_MEMORY;
+    sc->ctx = ctx;
+    sc->dim = d->dim;
+    sc->dtype = d->dtype;
+    sc->S = S;
+    sc->FO = d->fo_max;
+    sc->FR = d->fr_max;
+    sc->M_tot = M_tot;
+    sc->P_tot = P_tot;
+    sc->obs_C = d->obs_C;
+    sc->obs_d = d->obs_d;
+    sc->part_A = d->part_A;
+    sc->part_b = d->part_b;
+    sc->part_off = d->part_off;
+    sc->ny_max = d->fr_max + d->fo_max + 1;
+    sc->ns_max = d->dim == 3 ? 12 : 5;
+    sc->nu_max = d->dim == 3 ? 4 : 2;
+    sc->meta.resize(S);
+    sc->pair_begin.assign(S + 1, 0);
+    sc->state_begin.assign(S + 1, 0);
+    sc->ctrl_begin.assign(S + 1, 0);
+    long long qtot = 0, tiles = 0;
+    std::vector<long long> cost(S);
+    std::vector<int> Ms;
+    for (int s = 0; s < S; ++s) {
+        ScenMeta &m = sc->meta[s];
+        m.N = d->horizon[s];
+        m.M = d->obs_begin[s + 1] - d->obs_begin[s];
+        m.NP = d->part_begin[s + 1] - d->part_begin[s];
+        m.obs0 = d->obs_begin[s];
+        m.part0 = d->part_begin[s];
+        m.qbeg = (int)qtot;
+        m.state0 = (int)sc->state_begin[s];
+        m.ctrl0 = (int)sc->ctrl_begin[s];
+        m.tile0 = (int)tiles;
+        const int Q = m.NP * m.N;
+        m.ntile = (Q + 31) / 32;
+        m.pair0 = sc->pair_begin[s];
+        sc->pair_begin[s + 1] = sc->pair_begin[s] + (long long)m.M * Q;
+        sc->state_begin[s + 1] = sc->state_begin[s] + m.N + 1;
+        sc->ctrl_begin[s + 1] = sc->ctrl_begin[s] + m.N;
+        qtot += Q;
+        tiles += m.ntile;
+        sc->maxQ = std::max(sc->maxQ, Q);
+        sc->maxN = std::max(sc->maxN, m.N);
+        long long faces = 0;
+        for (int j = 0; j < m.M; ++j) faces += d->obs_nf[m.obs0 + j] + 1;
+        cost[s] = faces;
+        Ms.push_back(m.M);
+    }
+    if (qtot > (1LL << 30) || tiles > (1LL << 30) || sc->state_begin[S] > (1LL << 30)) {
+        free_scene(sc);
+        return OCA_ERR_CAPACITY;
+    }
+    sc->P = sc->pair_begin[S];
+    sc->n_states = sc->state_begin[S];
+    sc->n_ctrls = sc->ctrl_begin[S];
+    sc->Qtot = (int)qtot;
+    sc->n_tiles = (int)tiles;
+    // tiles in descending cost order (heaviest scenarios first)
+    std::vector<Tile> tl;
+    tl.reserve(tiles);
+    std::vector<int> order(S);
+    for (int s = 0; s < S; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    for (int s : order)
+        for (int k = 0; k < sc->meta[s].ntile; ++k) tl.push_back(Tile{s, 32 * k});
+    // warps per tile: about 8 obstacles per warp at the median obstacle count
+    std::nth_element(Ms.begin(), Ms.begin() + Ms.size() / 2, Ms.end());
+    const int Mmed = Ms[Ms.size() / 2];
+    sc->W = std::max(1, std::min(16, (Mmed + 7) / 8));
+
+    const size_t ts = dsize(d->dtype);
+    const int PK = d->dim + d->dim * d->dim;
+    const int NSTAT = d->dim * (d->dim + 1) / 2 + d->dim + d->dim * d->dim;
+    oca_status e = OCA_OK;
+    std::vector<long long> roff(S);
+    long long rtot = 0;
+    const int rkind = d->dim == 3 ? 2 : 1;
+    for (int s = 0; s < S; ++s) {
+        roff[s] = rtot;
+        rtot += riccati_scratch_elems(rkind, sc->meta[s].N);
+        rtot = (rtot + 3) & ~3LL;
+    }
+    if ((e = dmalloc(&sc->d_meta, sizeof(ScenMeta) * S)) != OCA_OK ||
+        (e = dmalloc(&sc->d_tiles, sizeof(Tile) * tl.size())) != OCA_OK ||
+        (e = dmalloc(&sc->d_obs_nf, sizeof(int) * M_tot)) != OCA_OK ||
+        (e = dmalloc(&sc->d_part_nf, sizeof(int) * P_tot)) != OCA_OK ||
+        (e = dmalloc(&sc->d_part_link, sizeof(int) * P_tot)) != OCA_OK ||
+        (e = dmalloc(&sc->d_part_radius, sizeof(double) * P_tot)) != OCA_OK ||
+        (e = dmalloc(&sc->d_pose, ts * PK * (size_t)qtot)) != OCA_OK ||
+        (e = dmalloc(&sc->d_stats, ts * NSTAT * (size_t)qtot)) != OCA_OK ||
+        (e = dmalloc(&sc->d_y2, ts * sc->ny_max * (size_t)sc->P)) != OCA_OK ||
+        (e = dmalloc(&sc->d_ric, sizeof(double) * (size_t)rtot)) != OCA_OK ||
+        (e = dmalloc(&sc->d_ric_off, sizeof(long long) * S)) != OCA_OK ||
+        (e = dmalloc(&sc->d_res, sizeof(double) * 4 * (size_t)tiles)) != OCA_OK ||
+        (e = dmalloc(&sc->d_status, sizeof(int) * S)) != OCA_OK ||
+        (e = dmalloc(&sc->d_iter, sizeof(int))) != OCA_OK ||
+        (e = dmalloc(&sc->d_active, sizeof(int))) != OCA_OK ||
+        (e = dmalloc(&sc->d_err, sizeof(int))) != OCA_OK ||
+        (e = dmalloc(&sc->d_box, ts * 2 * ((size_t)sc->n_states * sc->ns_max + (size_t)sc->n_ctrls * sc->nu_max))) != OCA_OK ||
+        (e = dmalloc(&sc->d_box_res, sizeof(double) * 2 * (size_t)S)) != OCA_OK) {
+        free_scene(sc);
+        return e;
+    }
+    if (cudaMallocHost(reinterpret_cast<void **>(&sc->h_active), sizeof(int)) != cudaSuccess) {
+        sc->h_active = nullptr;
+        free_scene(sc);
+        return OCA_ERR_NO_MEMORY;
+    }
+    bool ok = cudaMemcpy(sc->d_meta, sc->meta.data(), sizeof(ScenMeta) * S, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(sc->d_tiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(sc->d_obs_nf, d->obs_nf, sizeof(int) * M_tot, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(sc->d_part_nf, d->part_nf, sizeof(int) * P_tot, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(sc->d_part_link, d->part_link, sizeof(int) * P_tot, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(sc->d_ric_off, roff.data(), sizeof(long long) * S, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(sc->d_err, 0, sizeof(int)) == cudaSuccess &&
+              cudaMemset(sc->d_res, 0, sizeof(double) * 4 * (size_t)tiles) == cudaSuccess;
+    if (!ok) {
+        free_scene(sc);
+        return OCA_ERR_CUDA;
+    }
+    const int nthr = std::max(M_tot, P_tot);
+    if (d->dtype == OCA_F32)
+        k_validate<float><<<(nthr + 127) / 128, 128>>>(
+            static_cast<const float *>(d->obs_C), static_cast<const float *>(d->obs_d), sc->d_obs_nf, M_tot,
+            static_cast<const float *>(d->part_A), static_cast<const float *>(d->part_b), sc->d_part_nf, P_tot,
+            static_cast<const float *>(d->part_off), d->fo_max, d->fr_max, d->dim, sc->d_part_radius, sc->d_err);
+    else
+        k_validate<double><<<(nthr + 127) / 128, 128>>>(
+            static_cast<const double *>(d->obs_C), static_cast<const double *>(d->obs_d), sc->d_obs_nf, M_tot,
+            static_cast<const double *>(d->part_A), static_cast<const double *>(d->part_b), sc->d_part_nf, P_tot,
+            static_cast<const double *>(d->part_off), d->fo_max, d->fr_max, d->dim, sc->d_part_radius, sc->d_err);
+    int herr = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpy(&herr, sc->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        free_scene(sc);
+        return OCA_ERR_CUDA;
+    }
+    if (herr) {
+        free_scene(sc);
+        return OCA_ERR_INVALID_ARGUMENT;
+    }
+    *out = sc;
+    return OCA_OK;
+}
+
+void oca_scene_destroy(oca_scene *scene) { free_scene(scene); }
+
+oca_status oca_scene_info_get(const oca_scene *sc, oca_scene_info *info) {
+    if (!sc || !info) return OCA_ERR_INVALID_ARGUMENT;
+    info->n_pairs = sc->P;
+    info->n_states = sc->n_states;
+    info->n_ctrls = sc->n_ctrls;
+    info->ny_max = sc->ny_max;
+    info->n_tiles = sc->n_tiles;
+    info->pair_begin = sc->pair_begin.data();
+    info->state_begin = sc->state_begin.data();
+    info->ctrl_begin = sc->ctrl_begin.data();
+    return OCA_OK;
+}
+
+oca_status oca_scene_set_warps(oca_scene *sc, int warps) {
+    if (!sc || warps < 1 || warps > 16) return OCA_ERR_INVALID_ARGUMENT;
+    sc->W = warps;
+    return OCA_OK;
+}
+
+int oca_scene_get_warps(const oca_scene *sc) { return sc ? sc->W : -1; }
+
+oca_status oca_scale_detect_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model, const void *states,
+                                  void *alpha, void *lambda, void *mu, double *margin, int32_t *verdict,
+                                  int32_t *status, void *stream) {
+    if (!ctx || !scene || !states || !alpha) return OCA_ERR_INVALID_ARGUMENT;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    oca_status e = check_model(sc, model);
+    if (e != OCA_OK) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32)
+        return scale_impl<float>(sc, model, states, alpha, lambda, mu, margin, verdict, status, st);
+    return scale_impl<double>(sc, model, states, alpha, lambda, mu, margin, verdict, status, st);
+}
+
+oca_status oca_pair_qp_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model, const void *states,
+                             const void *zeta, const void *xi, double prox, const void *y_in, void *y_out,
+                             void *v_out, void *obj_out, int32_t *status_out, void *stream) {
+    if (!ctx || !scene || !states || !zeta || !xi || !y_in || !y_out) return OCA_ERR_INVALID_ARGUMENT;
+    if (!(prox >= 0.0) || !std::isfinite(prox)) return OCA_ERR_INVALID_ARGUMENT;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    oca_status e = check_model(sc, model);
+    if (e != OCA_OK) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32)
+        return pairqp_impl<float>(sc, model, states, zeta, xi, prox, y_in, y_out, v_out, obj_out, status_out, st);
+    return pairqp_impl<double>(sc, model, states, zeta, xi, prox, y_in, y_out, v_out, obj_out, status_out, st);
+}
+
+oca_status oca_admm_solve(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                          const oca_admm_params *params, const void *s_ref, void *s, void *u, void *y, void *zeta,
+                          void *xi, const oca_admm_report *report, void *stream) {
+    if (!ctx || !scene || !params || !s_ref || !s || !u || !y || !zeta || !xi || !report) return OCA_ERR_INVALID_ARGUMENT;
+    if (!report->iters || !report->status || !report->r_pri || !report->r_dual || !report->cost)
+        return OCA_ERR_INVALID_ARGUMENT;
+    if (!(params->sigma > 0.0) || !(params->prox >= 0.0) || !(params->eps_pri >= 0.0) || !(params->eps_dual >= 0.0) ||
+        params->max_iter < 0 || !std::isfinite(params->sigma) || !std::isfinite(params->prox) ||
+        !(params->rho_box >= 0.0) || !(params->damp >= 0.0) || !std::isfinite(params->rho_box) ||
+        !std::isfinite(params->damp))
+        return OCA_ERR_INVALID_ARGUMENT;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    oca_status e = check_model(sc, model);
+    if (e != OCA_OK) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32) return admm_impl<float>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st);
+    return admm_impl<double>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st);
+}
+
+}  // extern "C"

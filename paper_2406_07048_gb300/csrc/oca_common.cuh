@@ -1,0 +1,183 @@
+// Internal definitions shared by the CUDA translation units of liboca.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "oca.h"
+
+namespace oca {
+
+constexpr int kMaxFO = OCA_MAX_OBS_FACES;
+constexpr int kMaxFR = OCA_MAX_PART_FACES;
+constexpr int kActive = OCA_SCEN_ACTIVE;
+
+// Per-scenario metadata on the device.
+struct ScenMeta {
+    int N;       // horizon N_s (constraint steps t = 1..N)
+    int M;       // obstacles
+    int NP;      // robot parts
+    int obs0;    // first obstacle (global index)
+    int part0;   // first part (global index)
+    int qbeg;    // first (part, t) lane index; Q_s = NP * N lanes
+    int state0;  // first state row
+    int ctrl0;   // first control row
+    int tile0;   // first work tile (natural order)
+    int ntile;   // ceil(Q_s / 32)
+    long long pair0;  // first pair
+};
+
+// A work tile: 32 consecutive (part, t) lanes of one scenario.
+struct Tile {
+    int scen;
+    int q0;
+};
+
+// Scene geometry as kernels see it.
+template <typename T>
+struct Geom {
+    const T *obs_C;    // [M_tot][FO][D]
+    const T *obs_d;    // [M_tot][FO]
+    const int *obs_nf; // [M_tot]
+    const T *part_A;   // [P_tot][FR][D]
+    const T *part_b;   // [P_tot][FR]
+    const int *part_nf;
+    const int *part_link;
+    const T *part_off; // [P_tot][D]
+    int FO, FR;
+};
+
+template <typename T>
+struct DevModel {
+    int kind;
+    T dt;
+    T p[8];
+    T Qs[12];
+    T Qu[4];
+    T s_lo[12], s_hi[12];  // state box (|bound| >= 1e29: none)
+    T u_lo[4], u_hi[4];    // control box
+};
+
+template <int KIND> struct MDims;
+template <> struct MDims<0> { enum { NS = 4, NU = 2, D = 2, NROT = 1 }; };
+template <> struct MDims<1> { enum { NS = 5, NU = 2, D = 2, NROT = 1 }; };
+template <> struct MDims<2> { enum { NS = 12, NU = 4, D = 3, NROT = 3 }; };
+
+// pose record per (scenario, part, t): rho (D) then R (D*D, row-major)
+template <int D> struct PoseDims { enum { PK = D + D * D }; };
+// Gauss-Newton statistics per (scenario, part, t): W = sum w w^T (sym, D(D+1)/2),
+// Wc = sum c w (D), E = sum w e^T (D*D)
+template <int D> struct StatDims { enum { NW = D * (D + 1) / 2, NSTAT = D * (D + 1) / 2 + D + D * D }; };
+
+#define OCA_HD __host__ __device__
+
+// ---- math overloads --------------------------------------------------------
+OCA_HD inline float m_sin(float x) { return sinf(x); }
+OCA_HD inline double m_sin(double x) { return sin(x); }
+OCA_HD inline float m_cos(float x) { return cosf(x); }
+OCA_HD inline double m_cos(double x) { return cos(x); }
+OCA_HD inline float m_tan(float x) { return tanf(x); }
+OCA_HD inline double m_tan(double x) { return tan(x); }
+OCA_HD inline float m_sqrt(float x) { return sqrtf(x); }
+OCA_HD inline double m_sqrt(double x) { return sqrt(x); }
+OCA_HD inline float m_abs(float x) { return fabsf(x); }
+OCA_HD inline double m_abs(double x) { return fabs(x); }
+template <typename T> OCA_HD inline T m_eps();
+template <> OCA_HD inline float m_eps<float>() { return 1.1920929e-7f; }
+template <> OCA_HD inline double m_eps<double>() { return 2.220446049250313e-16; }
+OCA_HD inline bool m_finite(float x) { return isfinite(x); }
+OCA_HD inline bool m_finite(double x) { return isfinite(x); }
+
+template <typename T>
+OCA_HD inline T ldg(const T *p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+// ---- kernel argument blocks -------------------------------------------------
+template <typename T>
+struct PoseArgs {
+    const ScenMeta *meta;
+    int n_scen;
+    Geom<T> g;
+    DevModel<T> model;
+    const T *states;   // [n_states][NS]
+    T *pose;           // [PK][Qtot]
+    int Qtot;
+    const int *scen_status;  // may be null: then every scenario is posed
+};
+
+template <typename T>
+struct PairArgs {
+    const ScenMeta *meta;
+    const Tile *tiles;      // launch order (cost-sorted)
+    Geom<T> g;
+    const T *pose;          // [PK][Qtot]
+    int Qtot;
+    long long P;            // total pairs (component stride)
+    T *zeta;                // [P]
+    T *xi;                  // [D][P]
+    const T *y_in;          // [NY][P]
+    T *y_out;               // [NY][P]
+    T *v_out;               // [D+1][P] or null
+    T *obj_out;             // [P] or null
+    int *status_out;        // [P] or null
+    T *stats;               // [NSTAT][Qtot] (ADMM mode)
+    double *res;            // [2][n_tiles][2] residual partials (ADMM mode)
+    int n_tiles;
+    const int *scen_status; // ADMM mode
+    const int *iter;        // ADMM mode: device iteration counter j
+    int max_iter;
+    T prox;
+};
+
+template <typename T>
+struct ScaleArgs {
+    const ScenMeta *meta;
+    const Tile *tiles;
+    Geom<T> g;
+    const T *pose;
+    int Qtot;
+    long long P;
+    const double *part_radius;  // [P_tot] largest vertex norm of each part
+    T *alpha;
+    T *lambda;      // [FR][P] or null
+    T *mu;          // [FO][P] or null
+    double *margin; // [P] or null
+    int *verdict;   // [P] or null
+    int *status;    // [P] or null
+};
+
+template <typename T>
+struct RicArgs {
+    const ScenMeta *meta;
+    int n_scen;
+    Geom<T> g;
+    DevModel<T> model;
+    T sigma, eps_pri, eps_dual, rho_box, damp;
+    T *box_zs, *box_ws;  // [n_states][NS] bounded copy and scaled dual of the states
+    T *box_zu, *box_wu;  // [n_ctrls][NU]
+    double *box_res;     // [S][2] box residuals of the last trajectory step
+    int max_iter;
+    const int *iter;
+    const T *s_ref;
+    T *s;
+    T *u;
+    T *pose;
+    const T *stats;
+    int Qtot;
+    const double *res;  // [2][n_tiles][2]
+    int n_tiles;
+    int *scen_status;
+    int *status_out;
+    int *iters_out;
+    T *r_pri_out, *r_dual_out, *cost_out;
+    int *active_count;
+    void *scratch;      // per-stage workspace (factorisation precision)
+    const long long *scratch0;  // per-scenario offset into scratch (elements)
+};
+
+}  // namespace oca

@@ -1,0 +1,507 @@
+// Pair kernels: part poses, scale-LP collision detection and the fused
+// per-pair ADMM kernel (dual update, pair QP, dual residual, Gauss-Newton
+// statistics).
+//
+// Work decomposition ("obstacle sweep"): a CTA owns one tile = 32
+// consecutive (part, t) lanes of one scenario and W warps; warp w processes
+// obstacles j = w, w+W, ...  All lanes of a warp therefore work on the same
+// obstacle at the same time (its halfspaces are a broadcast load and its
+// face count is warp-uniform), pair arrays are read coalesced (pair index =
+// j*Q + q), and the per-(part, t) sums that the trajectory step needs are
+// accumulated in registers and reduced across the W warps in shared memory.
+#include <cfloat>
+
+#include "oca_common.cuh"
+#include "oca_kernels.h"
+#include "oca_models.cuh"
+#include "oca_solvers.cuh"
+
+namespace oca {
+
+// ============================================================================
+// poses (rho, R) of every (scenario, part, t = 1..N), Sec. IV-A
+// ============================================================================
+template <typename T, int KIND>
+__global__ void k_pose(PoseArgs<T> a) {
+    constexpr int D = MDims<KIND>::D, NS = MDims<KIND>::NS;
+    const int s = blockIdx.y;
+    const ScenMeta sm = a.meta[s];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= sm.NP * sm.N) return;
+    if (a.scen_status && a.scen_status[s] != kActive) return;
+    const int part = q / sm.N, t = q % sm.N + 1;
+    const int gp = sm.part0 + part;
+    T st[NS], off[D], rho[D], R[D * D];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) st[i] = a.states[(long long)(sm.state0 + t) * NS + i];
+#pragma unroll
+    for (int i = 0; i < D; ++i) off[i] = a.g.part_off[gp * D + i];
+    part_pose<T, KIND>(a.model, a.g.part_link[gp], off, st, rho, R, nullptr, nullptr, nullptr);
+    const int col = sm.qbeg + q;
+#pragma unroll
+    for (int i = 0; i < D; ++i) a.pose[(long long)i * a.Qtot + col] = rho[i];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) a.pose[(long long)(D + i) * a.Qtot + col] = R[i];
+}
+
+// ============================================================================
+// Fused pair kernel.
+//   MODE 0 (step 1 alone): y_out = QP(pose, zeta, xi, y_in); v, obj, status.
+//   MODE 1 (ADMM iteration j, Gauss-Seidel):
+//     head (j >= 1): zeta += T(s^j, y^j), xi += R(s^j, y^j)      [step 3 of j-1]
+//                    partial r_pri += T^2 + |R|^2
+//     qp   (j < max_iter): y^{j+1} = QP(s^j, zeta^j, xi^j; y^j) [step 1 of j]
+//                    partial r_dual += |dlambda|^2 + |dmu|^2
+//                    Gauss-Newton statistics of r = [T + zeta; R + xi] at
+//                    fixed y^{j+1}: W += w w^T, Wc += c w, E += w e^T with
+//                    w = C^T mu, c = 1 + d^T mu + gamma + zeta, e = A^T lambda + xi
+//     y buffers alternate by the parity of j (y_in = buf[j%2], y_out = buf[(j+1)%2]).
+// ============================================================================
+template <typename T, int D, int MODE, int SOLVER>
+__global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
+    constexpr int V = D + 1, SM = D + 2, PK = PoseDims<D>::PK, NSTAT = StatDims<D>::NSTAT, NW = StatDims<D>::NW;
+    extern __shared__ unsigned char smem_raw[];
+    T *red = reinterpret_cast<T *>(smem_raw);
+    const Tile tile = a.tiles[blockIdx.x];
+    const ScenMeta sm = a.meta[tile.scen];
+    int j_it = 0;
+    bool head = false, do_qp = true;
+    const T *y_in = a.y_in;
+    T *y_out = a.y_out;
+    if (MODE == 1) {
+        if (a.scen_status[tile.scen] != kActive) return;
+        j_it = *a.iter;
+        if (j_it > a.max_iter) return;
+        head = j_it >= 1;
+        do_qp = j_it < a.max_iter;
+        if (j_it & 1) {
+            y_in = a.y_out;
+            y_out = const_cast<T *>(a.y_in);
+        }
+    }
+    const int lane = threadIdx.x, warp = threadIdx.y, W = blockDim.y;
+    const int Q = sm.NP * sm.N;
+    const int q = tile.q0 + lane;
+    const bool valid = q < Q;
+    const long long P = a.P;
+    const int FR = a.g.FR, FO = a.g.FO;
+
+    Lane<T, D> L;
+    T st_W[NW], st_Wc[D], st_E[D * D];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) st_W[k] = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) st_Wc[k] = T(0);
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) st_E[k] = T(0);
+    double rp = 0.0, rd = 0.0;
+
+    if (valid) {
+        const int col = sm.qbeg + q;
+#pragma unroll
+        for (int i = 0; i < D; ++i) L.rho[i] = a.pose[(long long)i * a.Qtot + col];
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) L.R[i] = a.pose[(long long)(D + i) * a.Qtot + col];
+        const int gp = sm.part0 + q / sm.N;
+        L.A = a.g.part_A + (long long)gp * FR * D;
+        L.b = a.g.part_b + (long long)gp * FR;
+        L.nr = a.g.part_nf[gp];
+
+        for (int j = warp; j < sm.M; j += W) {
+            const int gm = sm.obs0 + j;
+            L.C = a.g.obs_C + (long long)gm * FO * D;
+            L.d = a.g.obs_d + (long long)gm * FO;
+            L.no = a.g.obs_nf[gm];
+            const long long p = sm.pair0 + (long long)j * Q + q;
+            const int ng = L.nr + L.no + 1;
+            T zeta = a.zeta[p];
+            T xi[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) xi[i] = a.xi[(long long)i * P + p];
+            const T *yb = y_in + p;
+            // ---- pass over y^j: compressed certificate and warm-start support
+            T a0[D], w0[D], del0 = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                a0[i] = T(0);
+                w0[i] = T(0);
+            }
+            Support<T, D> S;
+            S.n = 0;
+#pragma unroll
+            for (int k = 0; k < SM; ++k) {
+                S.id[k] = 0;
+                S.w[k] = T(0);
+            }
+            bool overflow = false;
+            T lam_sum = T(0);
+            for (int g = 0; g < ng; ++g) {
+                const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
+                const T yv = yb[(long long)c * P];
+                if (g < L.nr) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) a0[i] += yv * ldg(L.A + g * D + i);
+                } else if (g < L.nr + L.no) {
+                    const int m = g - L.nr;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) w0[i] += yv * ldg(L.C + m * D + i);
+                    del0 += yv * ldg(L.d + m);
+                } else {
+                    del0 += yv;
+                }
+                if (SOLVER == 0 && yv > T(0)) {
+                    const T wv = g < L.nr ? yv * ldg(L.b + g) : yv;
+                    if (g < L.nr) lam_sum += wv;
+                    if (S.n < SM) {
+#pragma unroll
+                        for (int k = 0; k < SM; ++k)
+                            if (k == S.n) {
+                                S.id[k] = g;
+                                S.w[k] = wv;
+                            }
+                        S.n += 1;
+                    } else {
+                        overflow = true;
+                    }
+                }
+            }
+            if (head) {
+                // step 3 of iteration j-1 at s^j: T = 1 + d'^T mu + gamma, R = A^T lambda + (C R)^T mu
+                T wr = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) wr += w0[i] * L.rho[i];
+                const T Tr = T(1) + del0 - wr;
+                zeta += Tr;
+                rp += double(Tr) * double(Tr);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    T acc = a0[i];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * w0[k];
+                    xi[i] += acc;
+                    rp += double(acc) * double(acc);
+                }
+                a.zeta[p] = zeta;
+#pragma unroll
+                for (int i = 0; i < D; ++i) a.xi[(long long)i * P + p] = xi[i];
+            }
+            if (!do_qp) continue;
+            T bq[V];
+            bq[0] = T(1) + zeta;
+#pragma unroll
+            for (int i = 0; i < D; ++i) bq[1 + i] = xi[i];
+            T v[V];
+            int status;
+            // ---- step 1: the pair QP
+            T ws[V], us[D];
+            SsnState<T, D> sst;
+            if (SOLVER == 0) {
+                if (overflow || S.n == 0 || !(lam_sum > T(0))) {
+                    sup_cold<T, D>(L, bq, S);
+                } else {
+                    const T il = T(1) / lam_sum;  // renormalise the lambda weights
+#pragma unroll
+                    for (int k = 0; k < SM; ++k)
+                        if (k < S.n && S.id[k] < L.nr) S.w[k] *= il;
+                }
+                status = mnp_solve<T, D>(L, S, bq, v);
+            } else {
+                // warm start: w0 = K^T y^j + bq at the current pose
+                T wr = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) wr += w0[i] * L.rho[i];
+                ws[0] = bq[0] + del0 - wr;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    T acc = bq[1 + i] + a0[i];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * w0[k];
+                    ws[1 + i] = acc;
+                }
+                status = ssn_solve<T, D>(L, yb, P, FR, FO, a.prox, bq, ws, sst);
+                for (int i_ = 0; i_ < D; ++i_) { T acc_ = T(0); for (int k_ = 0; k_ < D; ++k_) acc_ += L.R[i_ * D + k_] * ws[1 + k_]; us[i_] = acc_; }
+            }
+            // ---- write y^{j+1}; dual residual; compressed new certificate
+            T a1[D], w1[D], del1 = T(0), dy2 = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                a1[i] = T(0);
+                w1[i] = T(0);
+            }
+            T *yo = y_out + p;
+            for (int g = 0; g < ng; ++g) {
+                const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
+                T yv;
+                if (SOLVER == 0) {
+                    yv = T(0);
+#pragma unroll
+                    for (int k = 0; k < SM; ++k)
+                        if (k < S.n && S.id[k] == g) yv = S.w[k];
+                    if (g < L.nr) yv /= ldg(L.b + g);
+                } else {
+                    yv = ssn_value<T, D>(L, yb, P, FR, FO, a.prox, ws, us, sst.tau, g);
+                }
+                if (g < ng - 1) {
+                    const T dlt = yv - yb[(long long)c * P];
+                    dy2 += dlt * dlt;
+                }
+                yo[(long long)c * P] = yv;
+                if (g < L.nr) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) a1[i] += yv * ldg(L.A + g * D + i);
+                } else if (g < L.nr + L.no) {
+                    const int m = g - L.nr;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) w1[i] += yv * ldg(L.C + m * D + i);
+                    del1 += yv * ldg(L.d + m);
+                } else {
+                    del1 += yv;
+                }
+            }
+            if (SOLVER == 1) {
+                // v = K^T y + bq from the written y
+                T wr = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) wr += w1[i] * L.rho[i];
+                v[0] = bq[0] + del1 - wr;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    T acc = bq[1 + i] + a1[i];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * w1[k];
+                    v[1 + i] = acc;
+                }
+            }
+            if (MODE == 0) {
+                if (a.v_out) {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) a.v_out[(long long)i * P + p] = v[i];
+                }
+                if (a.obj_out) a.obj_out[p] = T(0.5) * dotv<T, V>(v, v);
+                if (a.status_out) a.status_out[p] = status;
+            } else {
+                rd += double(dy2);
+                const T cc = T(1) + del1 + zeta;
+                T e[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) e[i] = a1[i] + xi[i];
+                int k = 0;
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int jj = 0; jj <= i; ++jj) st_W[k++] += w1[i] * w1[jj];
+#pragma unroll
+                for (int i = 0; i < D; ++i) st_Wc[i] += cc * w1[i];
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < D; ++jj) st_E[i * D + jj] += w1[i] * e[jj];
+            }
+        }
+    }
+    if (MODE == 1) {
+        // ---- reduce statistics and residual partials across the W warps
+        T *rs = red;  // [W][NSTAT][32]
+        if (do_qp) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) rs[(warp * NSTAT + k) * 32 + lane] = st_W[k];
+#pragma unroll
+            for (int k = 0; k < D; ++k) rs[(warp * NSTAT + NW + k) * 32 + lane] = st_Wc[k];
+#pragma unroll
+            for (int k = 0; k < D * D; ++k) rs[(warp * NSTAT + NW + D + k) * 32 + lane] = st_E[k];
+        }
+        double *rr = reinterpret_cast<double *>(red + (size_t)W * NSTAT * 32);
+        // warp partials of the residuals
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rp += __shfl_xor_sync(0xffffffffu, rp, o);
+            rd += __shfl_xor_sync(0xffffffffu, rd, o);
+        }
+        if (lane == 0) {
+            rr[2 * warp] = rp;
+            rr[2 * warp + 1] = rd;
+        }
+        __syncthreads();
+        if (do_qp && valid) {
+            for (int k = warp; k < NSTAT; k += W) {
+                T acc = T(0);
+                for (int w2 = 0; w2 < W; ++w2) acc += rs[(w2 * NSTAT + k) * 32 + lane];
+                a.stats[(long long)k * a.Qtot + sm.qbeg + q] = acc;
+            }
+        }
+        if (warp == 0 && lane == 0) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int w2 = 0; w2 < W; ++w2) {
+                s1 += rr[2 * w2];
+                s2 += rr[2 * w2 + 1];
+            }
+            const int tn = sm.tile0 + tile.q0 / 32;
+            double *dst = a.res + (size_t)(j_it & 1) * a.n_tiles * 2 + (size_t)tn * 2;
+            dst[0] = s1;
+            dst[1] = s2;
+        }
+    }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(512) k_scale(ScaleArgs<T> a) {
+    constexpr int V = D + 1;
+    const Tile tile = a.tiles[blockIdx.x];
+    const ScenMeta sm = a.meta[tile.scen];
+    const int lane = threadIdx.x, warp = threadIdx.y, W = blockDim.y;
+    const int Q = sm.NP * sm.N;
+    const int q = tile.q0 + lane;
+    if (q >= Q) return;
+    const long long P = a.P;
+    const int FR = a.g.FR, FO = a.g.FO;
+    Lane<T, D> L;
+    const int col = sm.qbeg + q;
+#pragma unroll
+    for (int i = 0; i < D; ++i) L.rho[i] = a.pose[(long long)i * a.Qtot + col];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) L.R[i] = a.pose[(long long)(D + i) * a.Qtot + col];
+    const int gp = sm.part0 + q / sm.N;
+    L.A = a.g.part_A + (long long)gp * FR * D;
+    L.b = a.g.part_b + (long long)gp * FR;
+    L.nr = a.g.part_nf[gp];
+    for (int j = warp; j < sm.M; j += W) {
+        const int gm = sm.obs0 + j;
+        L.C = a.g.obs_C + (long long)gm * FO * D;
+        L.d = a.g.obs_d + (long long)gm * FO;
+        L.no = a.g.obs_nf[gm];
+        const long long p = sm.pair0 + (long long)j * Q + q;
+        int bas[V];
+        T xB[V], alpha;
+        int st = lp_solve<T, D>(L, bas, xB, alpha);
+        if (!(alpha == alpha)) st = OCA_PAIR_NONFINITE;
+        a.alpha[p] = alpha;
+        if (a.verdict) a.verdict[p] = alpha >= T(1) ? 1 : 0;
+        if (a.status) a.status[p] = st;
+        const int ART = L.nr + L.no;
+        if (a.lambda) {
+            for (int k = 0; k < L.nr; ++k) {
+                T v = T(0);
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (bas[i] == k) v = xB[i];
+                a.lambda[(long long)k * P + p] = v;
+            }
+        }
+        if (a.mu) {
+            for (int m = 0; m < L.no; ++m) {
+                T v = T(0);
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (bas[i] == L.nr + m) v = xB[i];
+                a.mu[(long long)m * P + p] = v;
+            }
+        }
+        if (a.margin) {
+            // FP64 weak-duality bound on alpha* from the certificate (lambda, mu)
+            double rho[D], R[D * D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) rho[i] = double(L.rho[i]);
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) R[i] = double(L.R[i]);
+            double bl = 0.0, dm = 0.0, r[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) r[i] = 0.0;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const int id = bas[i];
+                const double x = double(xB[i]);
+                if (id < L.nr) {
+                    bl += double(ldg(L.b + id)) * x;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) r[k] += double(ldg(L.A + id * D + k)) * x;
+                } else if (id < ART) {
+                    const int m = id - L.nr;
+                    double c[D], cr = 0.0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        c[k] = double(ldg(L.C + m * D + k));
+                        cr += c[k] * rho[k];
+                    }
+                    dm += (double(ldg(L.d + m)) - cr) * x;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        double cb = 0.0;
+#pragma unroll
+                        for (int l = 0; l < D; ++l) cb += R[l * D + k] * c[l];
+                        r[k] += cb * x;
+                    }
+                }
+            }
+            double rn = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) rn += r[k] * r[k];
+            const double den = bl + sqrt(rn) * a.part_radius[gp];
+            a.margin[p] = den > 0.0 ? -dm / den : -DBL_MAX;
+        }
+    }
+}
+
+// ============================================================================
+// launchers
+// ============================================================================
+template <typename T, int KIND>
+cudaError_t launch_pose_t(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
+    if (maxQ <= 0 || a.n_scen <= 0) return cudaSuccess;
+    dim3 grid((maxQ + 127) / 128, a.n_scen);
+    k_pose<T, KIND><<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
+    switch (a.model.kind) {
+        case 0: return launch_pose_t<T, 0>(a, maxQ, st);
+        case 1: return launch_pose_t<T, 1>(a, maxQ, st);
+        case 2: return launch_pose_t<T, 2>(a, maxQ, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int D>
+size_t pair_smem(int W) {
+    return (size_t)W * StatDims<D>::NSTAT * 32 * sizeof(T) + (size_t)W * 2 * sizeof(double);
+}
+
+template <typename T, int D, int MODE, int SOLVER>
+cudaError_t launch_pair_t(const PairArgs<T> &a, int n_tiles, int W, cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const size_t sm = MODE == 1 ? pair_smem<T, D>(W) : 0;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_pair<T, D, MODE, SOLVER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_pair<T, D, MODE, SOLVER><<<n_tiles, dim3(32, W), sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pair(const PairArgs<T> &a, int dim, int mode, int solver, int n_tiles, int W, cudaStream_t st) {
+#define OCA_PAIR_CASE(D_, M_, S_) \
+    if (dim == D_ && mode == M_ && solver == S_) return launch_pair_t<T, D_, M_, S_>(a, n_tiles, W, st);
+    OCA_PAIR_CASE(2, 0, 0) OCA_PAIR_CASE(2, 0, 1) OCA_PAIR_CASE(2, 1, 0) OCA_PAIR_CASE(2, 1, 1)
+    OCA_PAIR_CASE(3, 0, 0) OCA_PAIR_CASE(3, 0, 1) OCA_PAIR_CASE(3, 1, 0) OCA_PAIR_CASE(3, 1, 1)
+#undef OCA_PAIR_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_scale(const ScaleArgs<T> &a, int dim, int n_tiles, int W, cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (dim == 2) k_scale<T, 2><<<n_tiles, dim3(32, W), 0, st>>>(a);
+    else k_scale<T, 3><<<n_tiles, dim3(32, W), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_pose<float>(const PoseArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_pose<double>(const PoseArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_pair<float>(const PairArgs<float> &, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pair<double>(const PairArgs<double> &, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_scale<float>(const ScaleArgs<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_scale<double>(const ScaleArgs<double> &, int, int, int, cudaStream_t);
+
+}  // namespace oca
