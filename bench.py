@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the batched ADMM collision-avoidance solver on one GB300.
+
+A step is one whole ADMM solve (Sec. IV-B) of a batch of independent 2-D
+tractor-trailer scenarios shaped like the batching form (N ~ U[20,80],
+obstacles ~ U[8,64], 3-16 faces, 1-2 parts), from the same cold start, plus
+the scale-based collision check (Sec. III-A) of the returned plans.
+Metrics: pair-QP solves/s (value) and ADMM solves/s at residual <= 1e-4.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1: one process per GPU (torchrun, NCCL), each rank solving its own batch
+of scenarios (weak scaling, no data-path collective); timing is the max over
+ranks.  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-QP solves/s and ADMM solves/s at residual<=1e-4, batched FP32 vs plain GPU form"
+UNIT = "pair-QP solves/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons (read only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pair_bytes(scene, itemsize=4):
+    """Algorithmic bytes of one fused pair-kernel launch per scenario:
+    read and write zeta (1), xi (d) and y (n_y of each pair)."""
+    d = scene.dim
+    out = np.zeros(scene.n_scen)
+    for s in range(scene.n_scen):
+        N, NP = int(scene.horizon[s]), scene.n_parts(s)
+        m0, m1 = int(scene.obs_begin[s]), int(scene.obs_begin[s + 1])
+        p0 = int(scene.part_begin[s])
+        nr = scene.part_nf[p0:p0 + NP].sum()
+        ny = (scene.obs_nf[m0:m1].sum() + 1) * NP * N + nr * (m1 - m0) * N   # sum over pairs of n_y
+        P = (m1 - m0) * NP * N
+        out[s] = itemsize * (2 * (d + 1) * P + 2 * ny)
+    return out
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_2406_07048_gb300 import binding, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    S = args.scen
+    scene = synth.config3(n_scen=S, first=rank * S)
+    ctx = binding.Context(local)
+    ds = binding.DeviceScene(ctx, scene, torch.float32)
+    pb = binding.Problem(ds)
+    s0, u0, y0 = pb.s.clone(), pb.u.clone(), pb.y.clone()
+    params = dict(binding.DEFAULTS)
+    params["max_iter"] = args.max_iter
+
+    # --- autotune the warps per tile on the step-1 kernel at the initial state
+    tune = {}
+    for w in (1, 2, 4, 8, 16):
+        ds.warps = w
+        for _ in range(2):
+            binding.pair_qp(ds, pb.s, pb.zeta, pb.xi, y0, prox=params["prox"], y_out=pb.y, want_v=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            binding.pair_qp(ds, pb.s, pb.zeta, pb.xi, y0, prox=params["prox"], y_out=pb.y, want_v=False)
+        e1.record()
+        torch.cuda.synchronize()
+        tune[w] = e0.elapsed_time(e1) / 3
+    best_w = min(tune, key=tune.get)
+    ds.warps = best_w
+
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        pb.s.copy_(s0)
+        pb.u.copy_(u0)
+        pb.y.copy_(y0)
+        pb.zeta.zero_()
+        pb.xi.zero_()
+
+    def step():
+        reset()
+        rep = pb.solve(**params)
+        sd = binding.scale_detect(ds, pb.s, want_certificate=False, want_margin=False)
+        return rep, sd
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    bpp = pair_bytes(scene)
+    pc = scene.pair_counts.astype(np.float64)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = []
+    for _ in range(args.steps):
+        rep, sd = step()
+        reps.append({k: v.clone() for k, v in rep.items()})
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+
+    qp_solves, converged, algo_bytes = 0.0, 0, 0.0
+    iters_all = []
+    d1 = scene.dim + 1
+    ny_sum = (bpp / 4 - 2 * d1 * pc) / 2               # sum over a scenario's pairs of n_y
+    b_first = 4 * (d1 * pc + 2 * ny_sum)               # j = 0: zeta, xi read; y read and written
+    b_full = 4 * (2 * d1 * pc + 2 * ny_sum)            # dual update + QP: zeta, xi, y read and written
+    b_head = 4 * (2 * d1 * pc + ny_sum)                # dual update only (j = max_iter)
+    for rep in reps:
+        it = rep["iters"].cpu().numpy().astype(np.float64)
+        st = rep["status"].cpu().numpy()
+        qp_solves += float((pc * it).sum())
+        converged += int((st == 0).sum())
+        iters_all.append(it)
+        # a scenario retired at check j ran launches 0..j; one that reached
+        # max_iter ran 0..max_iter-1 in full and a dual-update-only launch
+        capped = st == 1
+        n_full = np.where(capped, np.maximum(it - 1, 0), it)
+        algo_bytes += float((b_first + n_full * b_full + capped * b_head).sum())
+    tot = np.array([qp_solves, converged, ms, algo_bytes, prof["pair_ms"], prof["traj_ms"], prof["pair_launches"]],
+                   dtype=np.float64)
+    if dist:
+        t = torch.tensor(tot, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tot = t.cpu().numpy()
+        ms = float(tmax[2].item())
+    value = tot[0] / (ms / 1e3)
+    admm_rate = tot[1] / (ms / 1e3)
+
+    # --- end to end through the public API with host buffers (pinned)
+    h_in = {k: v.cpu().pin_memory() for k, v in dict(s_ref=pb.s_ref, s=s0, u=u0, y=y0, zeta=torch.zeros_like(pb.zeta),
+                                                      xi=torch.zeros_like(pb.xi)).items()}
+    h_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in dict(s=pb.s, u=pb.u).items()}
+    h2d = sum(v.numel() * v.element_size() for v in h_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values()) + S * 4 * 2     # + iters and status
+    e_qp = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pb.s_ref.copy_(h_in["s_ref"], non_blocking=True)
+        pb.s.copy_(h_in["s"], non_blocking=True)
+        pb.u.copy_(h_in["u"], non_blocking=True)
+        pb.y.copy_(h_in["y"], non_blocking=True)
+        pb.zeta.copy_(h_in["zeta"], non_blocking=True)
+        pb.xi.copy_(h_in["xi"], non_blocking=True)
+        rep = pb.solve(**params)
+        h_out["s"].copy_(pb.s, non_blocking=True)
+        h_out["u"].copy_(pb.u, non_blocking=True)
+        it = rep["iters"].cpu().numpy()
+        rep["status"].cpu()
+        e_qp += float((pc * it).sum())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    # --- plain per-scenario GPU form (one scenario per call, legacy stream, no graphs)
+    plain = None
+    if rank == 0 and args.plain > 0:
+        idx = list(range(min(args.plain, S)))
+        sub_ms, sub_solves = 0.0, 0.0
+        for s in idx:
+            sc1 = synth.subset(scene, [s])
+            d1s = binding.DeviceScene(ctx, sc1, torch.float32)
+            p1 = binding.Problem(d1s)
+            p1.solve(**params)  # warm the path
+            p1 = binding.Problem(d1s)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r1 = binding.admm_solve(d1s, p1.s_ref, p1.s, p1.u, p1.y, p1.zeta, p1.xi, stream=torch.cuda.default_stream(),
+                                    **params)
+            torch.cuda.synchronize()
+            sub_ms += (time.perf_counter() - t0) * 1e3
+            sub_solves += float(sc1.pair_counts[0] * int(r1["iters"][0]))
+            d1s.close()
+        plain = {"scenarios_timed": len(idx), "ms_per_scenario": sub_ms / len(idx),
+                 "pair_qp_solves_per_s": sub_solves / (sub_ms / 1e3),
+                 "batched_speedup": (sub_ms / len(idx)) / (ms / args.steps / S)}
+
+    peak, peak_kind = _peaks()
+    achieved = tot[3] / (tot[4] / 1e3) / 1e9 if tot[4] > 0 else 0.0
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "k_pair_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            tj = json.load(f)
+        if tj.get("kernel_sha") == _kernel_sha():
+            traffic = tj.get("bytes_per_launch_full_workload")
+    # per step: reset, 2 box inits, poses, gather, scale-detect poses + LP = 7,
+    # and per iteration launch: pair kernel, trajectory kernel, counter advance
+    launches = int(7 * args.steps * world + 3 * tot[6])
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batching form, 2-D tractor-trailer, {S} scenarios per GPU (N~U[20,80], "
+                               f"obstacles~U[8,64], 3-16 faces, 1-2 parts), cold start, max_iter {args.max_iter}",
+                   "scenarios_per_gpu": S, "pairs_per_gpu": int(scene.n_pairs),
+                   "admm": {k: params[k] for k in ("sigma", "eps_pri", "eps_dual", "prox", "rho_box", "damp")},
+                   "precision": "pair QPs / residuals / duals FP32, Riccati factorisation FP64",
+                   "warps_per_tile": best_w, "tuner_ms": {str(k): round(v, 4) for k, v in tune.items()},
+                   "l2": "inputs larger than L2 (y alone %.0f MB)" % (pb.y.numel() * 4 / 1e6),
+                   "parallelism": f"scenario shards x{world}"},
+        "admm_solves_per_s": admm_rate,
+        "converged_fraction": tot[1] / (S * world * args.steps),
+        "mean_iterations": float(np.mean(np.concatenate(iters_all))),
+        "kernel_ms": {"pair": tot[4], "trajectory": tot[5], "pair_launches": int(tot[6])},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair (fused dual update + pair QP)",
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
+        "e2e": {"value": e_qp / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "plain_form": plain,
+    }
+    if clk:
+        out["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scene, params, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _kernel_sha():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("oca_pair.cu", "oca_solvers.cuh", "oca_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_07048_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def cpu_baseline(scene, params, seconds):
+    """The FP64 oracle as it stands on a bounded sample of the workload."""
+    import oracle
+    from paper_2406_07048_gb300 import synth
+    oracle.build()
+    cores = oracle.num_threads()
+    done, solves, conv = 0, 0.0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done < scene.n_scen:
+        idx = list(range(done, min(done + cores, scene.n_scen)))
+        sub = synth.subset(scene, idx)
+        r = oracle.admm_batch(sub, nthreads=cores, **{k: params[k] for k in
+                                                       ("sigma", "eps_pri", "eps_dual", "prox", "max_iter",
+                                                        "rho_box", "damp")})
+        solves += float((sub.pair_counts * r["iters"]).sum())
+        conv += int((r["status"] == 0).sum())
+        done += len(idx)
+    el = time.perf_counter() - t0
+    return {"value": solves / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of the {scene.n_scen} scenarios, whole ADMM solves, {el:.1f} s",
+            "admm_solves_per_s": conv / el}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2406_07048_gb300 import binding, synth
+    oracle.build()
+    cores = oracle.num_threads()
+    S = args.scen
+    scene = synth.config3(n_scen=S)
+    params = dict(binding.DEFAULTS)
+    params["max_iter"] = args.max_iter
+    kw = {k: params[k] for k in ("sigma", "eps_pri", "eps_dual", "prox", "max_iter", "rho_box", "damp")}
+    per_step = max(1, cores)
+
+    def one(step_i):
+        idx = [(step_i * per_step + k) % S for k in range(per_step)]
+        sub = synth.subset(scene, idx)
+        r = oracle.admm_batch(sub, nthreads=cores, **kw)
+        return float((sub.pair_counts * r["iters"]).sum()), int((r["status"] == 0).sum())
+
+    for w in range(args.warmup):
+        one(w)
+    t0 = time.perf_counter()
+    solves, conv = 0.0, 0
+    for k in range(args.steps):
+        a, b = one(args.warmup + k)
+        solves += a
+        conv += b
+    el = time.perf_counter() - t0
+    v = solves / el
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"batching form, 2-D tractor-trailer, {S} scenarios (bounded sample of "
+                                  f"{per_step} scenarios per step on the host cores)", "max_iter": args.max_iter},
+           "admm_solves_per_s": conv / el,
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{per_step} scenarios per step, {args.steps} steps"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scen", type=int, default=2048)
+    ap.add_argument("--max-iter", type=int, default=300)
+    ap.add_argument("--plain", type=int, default=16, help="scenarios timed in the plain per-scenario form")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

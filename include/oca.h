@@ -238,6 +238,24 @@ oca_status oca_admm_solve(oca_ctx *ctx, const oca_scene *scene, const oca_model 
                           void *y, void *zeta, void *xi, const oca_admm_report *report,
                           void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Kernel timing                                                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double pair_ms;        /* summed device time of the fused pair kernel launches */
+    double traj_ms;        /* summed device time of the trajectory (Riccati) launches */
+    int64_t pair_launches; /* launches that did work (iteration index <= max_iter) */
+    int64_t traj_launches;
+} oca_profile_stats;
+
+/* Start (enable != 0) or stop timing oca_admm_solve's kernels on this
+ * context with CUDA events recorded around each launch (also inside the
+ * captured iteration graphs); starting resets the counters.  The events are
+ * read when the host tests for convergence between iteration chunks, so the
+ * timed solve runs in its normal configuration.  Errors: OCA_ERR_CUDA. */
+oca_status oca_profile_enable(oca_ctx *ctx, int enable);
+oca_status oca_profile_read(const oca_ctx *ctx, oca_profile_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,11 @@ class AdmmParams(C.Structure):
                 ("max_iter", C.c_int32), ("flags", C.c_int32), ("rho_box", C.c_double), ("damp", C.c_double)]
 
 
+class ProfileStats(C.Structure):
+    _fields_ = [("pair_ms", C.c_double), ("traj_ms", C.c_double), ("pair_launches", C.c_int64),
+                ("traj_launches", C.c_int64)]
+
+
 class Report(C.Structure):
     _fields_ = [("iters", C.c_void_p), ("status", C.c_void_p), ("r_pri", C.c_void_p), ("r_dual", C.c_void_p),
                 ("cost", C.c_void_p)]
@@ -64,7 +69,7 @@ class Report(C.Structure):
 
 EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create", "oca_scene_destroy",
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
-            "oca_pair_qp_batch", "oca_admm_solve"]
+            "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read"]
 
 
 def lib():
@@ -98,6 +103,10 @@ def lib():
         L.oca_admm_solve.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, P, P, P, P,
                                      C.POINTER(Report), P]
         L.oca_admm_solve.restype = I
+        L.oca_profile_enable.argtypes = [P, I]
+        L.oca_profile_enable.restype = I
+        L.oca_profile_read.argtypes = [P, C.POINTER(ProfileStats)]
+        L.oca_profile_read.restype = I
         _lib = L
     return _lib
 
@@ -149,6 +158,15 @@ class Context:
         h = C.c_void_p()
         _check(lib().oca_create(C.byref(h), int(device)), "oca_create")
         self.h = h
+
+    def profile(self, enable: bool = True):
+        _check(lib().oca_profile_enable(self.h, int(bool(enable))), "oca_profile_enable")
+
+    def profile_read(self) -> dict:
+        ps = ProfileStats()
+        _check(lib().oca_profile_read(self.h, C.byref(ps)), "oca_profile_read")
+        return dict(pair_ms=ps.pair_ms, traj_ms=ps.traj_ms, pair_launches=ps.pair_launches,
+                    traj_launches=ps.traj_launches)
 
     def close(self):
         if self.h:
@@ -255,10 +273,10 @@ def pair_qp(ds: DeviceScene, states, zeta, xi, y_in, prox: float = 0.0, y_out=No
     return dict(y=y_out, v=v, obj=obj, status=status)
 
 
-DEFAULTS = dict(sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1e-2, max_iter=300, rho_box=100.0, damp=100.0)
+DEFAULTS = dict(sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.1, max_iter=300, rho_box=100.0, damp=100.0)
 
 
-def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1e-2,
+def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.1,
                max_iter=300, flags=0, rho_box=100.0, damp=100.0, stream=None):
     """oca_admm_solve: updates s, u, y, zeta, xi in place; returns the report."""
     S = ds.scene.n_scen

@@ -16,6 +16,11 @@ using namespace oca;
 struct oca_ctx {
     int device;
     int n_sm;
+    // kernel timing (oca_profile_enable)
+    bool prof = false;
+    cudaEvent_t ev[4][8] = {};  // [pair start, pair stop, traj start, traj stop][iteration in chunk]
+    double pair_ms = 0, traj_ms = 0;
+    long long pair_launches = 0, traj_launches = 0;
 };
 
 struct oca_scene {
@@ -370,11 +375,22 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     r.scratch0 = sc->d_ric_off;
     const bool f32 = (pr->flags & OCA_ADMM_RICCATI_F32) != 0 && sizeof(T) == sizeof(float);
 
-    auto one_iter = [&]() -> cudaError_t {
-        cudaError_t e = launch_pair<T>(a, sc->dim, 1, solver, sc->n_tiles, sc->W, st);
+    oca_ctx *cx = sc->ctx;
+    const bool prof = cx->prof;
+    bool capturing = false;
+    auto rec = [&](cudaEvent_t e) -> cudaError_t {
+        return capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+    };
+    auto one_iter = [&](int k) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (prof && (e = rec(cx->ev[0][k])) != cudaSuccess) return e;
+        e = launch_pair<T>(a, sc->dim, 1, solver, sc->n_tiles, sc->W, st);
         if (e != cudaSuccess) return e;
+        if (prof && (e = rec(cx->ev[1][k])) != cudaSuccess) return e;
+        if (prof && (e = rec(cx->ev[2][k])) != cudaSuccess) return e;
         e = launch_riccati<T>(r, f32, st);
         if (e != cudaSuccess) return e;
+        if (prof && (e = rec(cx->ev[3][k])) != cudaSuccess) return e;
         k_advance<<<1, 1, 0, st>>>(sc->d_iter);
         return cudaGetLastError();
     };
@@ -384,8 +400,10 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     if (st != nullptr && n_launch > G) {
         cudaGraph_t graph = nullptr;
         OCA_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
         cudaError_t ce = cudaSuccess;
-        for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = one_iter();
+        for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = one_iter(k);
+        capturing = false;
         cudaError_t ee = cudaStreamEndCapture(st, &graph);
         if (ce != cudaSuccess || ee != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -396,18 +414,35 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
         if (ie != cudaSuccess) return OCA_ERR_CUDA;
     }
     oca_status out = OCA_OK;
+    *sc->h_active = sc->S;
     for (long long done = 0; done < n_launch; done += G) {
         if (exec) {
             if (cudaGraphLaunch(exec, st) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
         } else {
             for (int k = 0; k < G && done + k < n_launch; ++k)
-                if (one_iter() != cudaSuccess) { out = OCA_ERR_CUDA; break; }
+                if (one_iter(k) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
             if (out != OCA_OK) break;
         }
         if (cudaMemcpyAsync(sc->h_active, sc->d_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             out = OCA_ERR_CUDA;
             break;
+        }
+        if (prof) {
+            const long long nk = std::min<long long>(G, n_launch - done);
+            for (long long k = 0; k < nk; ++k) {
+                float m1 = 0.f, m2 = 0.f;
+                if (cudaEventElapsedTime(&m1, cx->ev[0][k], cx->ev[1][k]) != cudaSuccess ||
+                    cudaEventElapsedTime(&m2, cx->ev[2][k], cx->ev[3][k]) != cudaSuccess) {
+                    out = OCA_ERR_CUDA;
+                    break;
+                }
+                cx->pair_ms += m1;
+                cx->traj_ms += m2;
+                cx->pair_launches += 1;
+                cx->traj_launches += 1;
+            }
+            if (out != OCA_OK) break;
         }
         if (*sc->h_active <= 0) break;
     }
@@ -484,7 +519,35 @@ oca_status oca_create(oca_ctx **out, int device) {
     return OCA_OK;
 }
 
-void oca_destroy(oca_ctx *ctx) { delete ctx; }
+void oca_destroy(oca_ctx *ctx) {
+    if (!ctx) return;
+    for (auto &row : ctx->ev)
+        for (auto &e : row)
+            if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+oca_status oca_profile_enable(oca_ctx *ctx, int enable) {
+    if (!ctx) return OCA_ERR_INVALID_ARGUMENT;
+    if (enable) {
+        for (auto &row : ctx->ev)
+            for (auto &e : row)
+                if (!e && cudaEventCreate(&e) != cudaSuccess) return OCA_ERR_CUDA;
+        ctx->pair_ms = ctx->traj_ms = 0;
+        ctx->pair_launches = ctx->traj_launches = 0;
+    }
+    ctx->prof = enable != 0;
+    return OCA_OK;
+}
+
+oca_status oca_profile_read(const oca_ctx *ctx, oca_profile_stats *out) {
+    if (!ctx || !out) return OCA_ERR_INVALID_ARGUMENT;
+    out->pair_ms = ctx->pair_ms;
+    out->traj_ms = ctx->traj_ms;
+    out->pair_launches = ctx->pair_launches;
+    out->traj_launches = ctx->traj_launches;
+    return OCA_OK;
+}
 
 oca_status oca_scene_create(oca_ctx *ctx, const oca_scene_desc *d, oca_scene **out) {
     if (!ctx || !d || !out) return OCA_ERR_INVALID_ARGUMENT;

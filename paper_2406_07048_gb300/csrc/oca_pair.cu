@@ -57,11 +57,10 @@ __global__ void k_pose(PoseArgs<T> a) {
 //                    w = C^T mu, c = 1 + d^T mu + gamma + zeta, e = A^T lambda + xi
 //     y buffers alternate by the parity of j (y_in = buf[j%2], y_out = buf[(j+1)%2]).
 // ============================================================================
-template <typename T, int D, int MODE, int SOLVER>
+template <typename T, int D, int MODE, int SOLVER, int NR>
 __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
-    constexpr int V = D + 1, SM = D + 2, PK = PoseDims<D>::PK, NSTAT = StatDims<D>::NSTAT, NW = StatDims<D>::NW;
-    extern __shared__ unsigned char smem_raw[];
-    T *red = reinterpret_cast<T *>(smem_raw);
+    constexpr int V = D + 1, SM = D + 2, NSTAT = StatDims<D>::NSTAT, NW = StatDims<D>::NW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Tile tile = a.tiles[blockIdx.x];
     const ScenMeta sm = a.meta[tile.scen];
     int j_it = 0;
@@ -80,13 +79,18 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
         }
     }
     const int lane = threadIdx.x, warp = threadIdx.y, W = blockDim.y;
+    const int BT = 32 * W, tid = warp * 32 + lane;
     const int Q = sm.NP * sm.N;
     const int q = tile.q0 + lane;
     const bool valid = q < Q;
     const long long P = a.P;
     const int FR = a.g.FR, FO = a.g.FO;
+    // shared memory: [staged face data 4 x FO x BT] [statistics W x NSTAT x 32] [residuals W x 2 (double)]
+    T *stg = reinterpret_cast<T *>(smem_raw);
+    T *red = stg + (SOLVER == 1 ? 4 * FO * BT : 0);
 
     Lane<T, D> L;
+    SsnLane<T, D, NR> SL;
     T st_W[NW], st_Wc[D], st_E[D * D];
 #pragma unroll
     for (int k = 0; k < NW; ++k) st_W[k] = T(0);
@@ -106,6 +110,37 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
         L.A = a.g.part_A + (long long)gp * FR * D;
         L.b = a.g.part_b + (long long)gp * FR;
         L.nr = a.g.part_nf[gp];
+        const T rho_p = a.prox;
+        if constexpr (SOLVER == 1) {
+            // robot-part constants of the proximal metric (registers)
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) SL.R[i] = L.R[i];
+            SL.nr = L.nr;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                T a2 = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    SL.a[k][i] = k < L.nr ? ldg(L.A + k * D + i) : T(0);
+                    a2 += SL.a[k][i] * SL.a[k][i];
+                }
+                const T bk = k < L.nr ? ldg(L.b + k) : T(1);
+                if (!(a2 > T(0))) a2 = T(1);
+                SL.b[k] = bk;
+                SL.iD[k] = T(1) / a2;
+                SL.iDr[k] = SL.iD[k] / rho_p;
+                SL.Db[k] = a2 / bk;
+                SL.bD[k] = bk * SL.iD[k];
+                SL.b2D[k] = bk * SL.bD[k];
+                SL.rD[k] = rho_p * a2;
+                SL.yl[k] = T(0);
+            }
+            SL.BT = BT;
+            SL.sdp = stg + tid;
+            SL.siD = stg + FO * BT + tid;
+            SL.syb = stg + 2 * FO * BT + tid;
+            SL.sq = stg + 3 * FO * BT + tid;
+        }
 
         for (int j = warp; j < sm.M; j += W) {
             const int gm = sm.obs0 + j;
@@ -119,7 +154,9 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
 #pragma unroll
             for (int i = 0; i < D; ++i) xi[i] = a.xi[(long long)i * P + p];
             const T *yb = y_in + p;
-            // ---- pass over y^j: compressed certificate and warm-start support
+            T *yo = y_out + p;
+            // ---- one pass over y^j: compressed certificate (A^T lambda, C^T mu,
+            // d^T mu + gamma), warm-start support or staged face data
             T a0[D], w0[D], del0 = T(0);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
@@ -135,33 +172,68 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
             }
             bool overflow = false;
             T lam_sum = T(0);
-            for (int g = 0; g < ng; ++g) {
-                const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
-                const T yv = yb[(long long)c * P];
-                if (g < L.nr) {
+            if constexpr (SOLVER == 1) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) a0[i] += yv * ldg(L.A + g * D + i);
-                } else if (g < L.nr + L.no) {
-                    const int m = g - L.nr;
+                for (int k = 0; k < NR; ++k) {
+                    if (k < L.nr) {
+                        const T yv = yb[(long long)k * P];
+                        SL.yl[k] = yv;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) w0[i] += yv * ldg(L.C + m * D + i);
-                    del0 += yv * ldg(L.d + m);
-                } else {
-                    del0 += yv;
+                        for (int i = 0; i < D; ++i) a0[i] += yv * SL.a[k][i];
+                    }
                 }
-                if (SOLVER == 0 && yv > T(0)) {
-                    const T wv = g < L.nr ? yv * ldg(L.b + g) : yv;
-                    if (g < L.nr) lam_sum += wv;
-                    if (S.n < SM) {
+                for (int m = 0; m < L.no; ++m) {
+                    const T yv = yb[(long long)(FR + m) * P];
+                    T c[D], cr = T(0), c2 = T(0);
 #pragma unroll
-                        for (int k = 0; k < SM; ++k)
-                            if (k == S.n) {
-                                S.id[k] = g;
-                                S.w[k] = wv;
-                            }
-                        S.n += 1;
+                    for (int i = 0; i < D; ++i) {
+                        c[i] = ldg(L.C + m * D + i);
+                        w0[i] += yv * c[i];
+                        cr += c[i] * L.rho[i];
+                        c2 += c[i] * c[i];
+                    }
+                    const T dm = ldg(L.d + m);
+                    del0 += yv * dm;
+                    const T dp = dm - cr;
+                    const T Dm = dp * dp + c2;
+                    const T iDm = T(1) / (rho_p * Dm);
+                    const int o = m * BT + tid;
+                    stg[o] = dp;
+                    stg[FO * BT + o] = iDm;
+                    stg[2 * FO * BT + o] = yv;
+                    stg[3 * FO * BT + o] = rho_p * Dm * yv * yv;
+                }
+                SL.ybg = yb[(long long)(FR + FO) * P];
+                del0 += SL.ybg;
+            } else {
+                for (int g = 0; g < ng; ++g) {
+                    const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
+                    const T yv = yb[(long long)c * P];
+                    if (g < L.nr) {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) a0[i] += yv * ldg(L.A + g * D + i);
+                    } else if (g < L.nr + L.no) {
+                        const int m = g - L.nr;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) w0[i] += yv * ldg(L.C + m * D + i);
+                        del0 += yv * ldg(L.d + m);
                     } else {
-                        overflow = true;
+                        del0 += yv;
+                    }
+                    if (yv > T(0)) {
+                        const T wv = g < L.nr ? yv * ldg(L.b + g) : yv;
+                        if (g < L.nr) lam_sum += wv;
+                        if (S.n < SM) {
+#pragma unroll
+                            for (int k = 0; k < SM; ++k)
+                                if (k == S.n) {
+                                    S.id[k] = g;
+                                    S.w[k] = wv;
+                                }
+                            S.n += 1;
+                        } else {
+                            overflow = true;
+                        }
                     }
                 }
             }
@@ -192,10 +264,14 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
             for (int i = 0; i < D; ++i) bq[1 + i] = xi[i];
             T v[V];
             int status;
-            // ---- step 1: the pair QP
-            T ws[V], us[D];
-            SsnState<T, D> sst;
-            if (SOLVER == 0) {
+            T a1[D], w1[D], del1 = T(0), dy2 = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                a1[i] = T(0);
+                w1[i] = T(0);
+            }
+            if constexpr (SOLVER == 0) {
+                // ---- step 1 by the active-set method, warm-started from y^j's support
                 if (overflow || S.n == 0 || !(lam_sum > T(0))) {
                     sup_cold<T, D>(L, bq, S);
                 } else {
@@ -205,8 +281,33 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
                         if (k < S.n && S.id[k] < L.nr) S.w[k] *= il;
                 }
                 status = mnp_solve<T, D>(L, S, bq, v);
+                for (int g = 0; g < ng; ++g) {
+                    const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
+                    T yv = T(0);
+#pragma unroll
+                    for (int k = 0; k < SM; ++k)
+                        if (k < S.n && S.id[k] == g) yv = S.w[k];
+                    if (g < L.nr) yv /= ldg(L.b + g);
+                    if (g < ng - 1) {
+                        const T dlt = yv - yb[(long long)c * P];
+                        dy2 += dlt * dlt;
+                    }
+                    yo[(long long)c * P] = yv;
+                    if (g < L.nr) {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) a1[i] += yv * ldg(L.A + g * D + i);
+                    } else if (g < L.nr + L.no) {
+                        const int m = g - L.nr;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) w1[i] += yv * ldg(L.C + m * D + i);
+                        del1 += yv * ldg(L.d + m);
+                    } else {
+                        del1 += yv;
+                    }
+                }
             } else {
-                // warm start: w0 = K^T y^j + bq at the current pose
+                // ---- step 1 by semismooth Newton, warm-started at w0 = K^T y^j + bq
+                T ws[V];
                 T wr = T(0);
 #pragma unroll
                 for (int i = 0; i < D; ++i) wr += w0[i] * L.rho[i];
@@ -218,52 +319,54 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
                     for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * w0[k];
                     ws[1 + i] = acc;
                 }
-                status = ssn_solve<T, D>(L, yb, P, FR, FO, a.prox, bq, ws, sst);
-                for (int i_ = 0; i_ < D; ++i_) { T acc_ = T(0); for (int k_ = 0; k_ < D; ++k_) acc_ += L.R[i_ * D + k_] * ws[1 + k_]; us[i_] = acc_; }
-            }
-            // ---- write y^{j+1}; dual residual; compressed new certificate
-            T a1[D], w1[D], del1 = T(0), dy2 = T(0);
+                SL.no = L.no;
+                SL.C = L.C;
+                SsnEval<T, D, NR> est;
+                status = ssn_solve_staged<T, D, NR>(SL, rho_p, bq, ws, est);
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                a1[i] = T(0);
-                w1[i] = T(0);
-            }
-            T *yo = y_out + p;
-            for (int g = 0; g < ng; ++g) {
-                const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
-                T yv;
-                if (SOLVER == 0) {
-                    yv = T(0);
+                for (int k = 0; k < NR; ++k) {
+                    if (k < L.nr) {
+                        const T yv = est.lam[k];
+                        const T dlt = yv - SL.yl[k];
+                        dy2 += dlt * dlt;
+                        yo[(long long)k * P] = yv;
 #pragma unroll
-                    for (int k = 0; k < SM; ++k)
-                        if (k < S.n && S.id[k] == g) yv = S.w[k];
-                    if (g < L.nr) yv /= ldg(L.b + g);
-                } else {
-                    yv = ssn_value<T, D>(L, yb, P, FR, FO, a.prox, ws, us, sst.tau, g);
+                        for (int i = 0; i < D; ++i) a1[i] += yv * SL.a[k][i];
+                    }
                 }
-                if (g < ng - 1) {
-                    const T dlt = yv - yb[(long long)c * P];
+                T Rw[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc += L.R[i * D + k] * ws[1 + k];
+                    Rw[i] = acc;
+                }
+                for (int m = 0; m < L.no; ++m) {
+                    const int o = m * BT + tid;
+                    const T dp = stg[o], iDm = stg[FO * BT + o], ybm = stg[2 * FO * BT + o];
+                    T c[D], cw = T(0);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        c[i] = ldg(L.C + m * D + i);
+                        cw += c[i] * Rw[i];
+                    }
+                    const T yv = fmax(T(0), ybm - (ws[0] * dp + cw) * iDm);
+                    const T dlt = yv - ybm;
                     dy2 += dlt * dlt;
-                }
-                yo[(long long)c * P] = yv;
-                if (g < L.nr) {
+                    yo[(long long)(FR + m) * P] = yv;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) a1[i] += yv * ldg(L.A + g * D + i);
-                } else if (g < L.nr + L.no) {
-                    const int m = g - L.nr;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) w1[i] += yv * ldg(L.C + m * D + i);
+                    for (int i = 0; i < D; ++i) w1[i] += yv * c[i];
                     del1 += yv * ldg(L.d + m);
-                } else {
-                    del1 += yv;
                 }
-            }
-            if (SOLVER == 1) {
+                const T gv = fmax(T(0), SL.ybg - ws[0] / rho_p);
+                yo[(long long)(FR + FO) * P] = gv;
+                del1 += gv;
                 // v = K^T y + bq from the written y
-                T wr = T(0);
+                T wr1 = T(0);
 #pragma unroll
-                for (int i = 0; i < D; ++i) wr += w1[i] * L.rho[i];
-                v[0] = bq[0] + del1 - wr;
+                for (int i = 0; i < D; ++i) wr1 += w1[i] * L.rho[i];
+                v[0] = bq[0] + del1 - wr1;
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
                     T acc = bq[1 + i] + a1[i];
@@ -311,7 +414,6 @@ __global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
             for (int k = 0; k < D * D; ++k) rs[(warp * NSTAT + NW + D + k) * 32 + lane] = st_E[k];
         }
         double *rr = reinterpret_cast<double *>(red + (size_t)W * NSTAT * 32);
-        // warp partials of the residuals
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             rp += __shfl_xor_sync(0xffffffffu, rp, o);
@@ -463,29 +565,37 @@ cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
 }
 
 template <typename T, int D>
-size_t pair_smem(int W) {
-    return (size_t)W * StatDims<D>::NSTAT * 32 * sizeof(T) + (size_t)W * 2 * sizeof(double);
+size_t pair_smem(int W, int mode, int solver, int FO) {
+    size_t b = 0;
+    if (solver == 1) b += (size_t)4 * FO * 32 * W * sizeof(T);
+    if (mode == 1) b += (size_t)W * StatDims<D>::NSTAT * 32 * sizeof(T) + (size_t)W * 2 * sizeof(double);
+    return b;
 }
 
-template <typename T, int D, int MODE, int SOLVER>
+template <typename T, int D, int MODE, int SOLVER, int NR>
 cudaError_t launch_pair_t(const PairArgs<T> &a, int n_tiles, int W, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    const size_t sm = MODE == 1 ? pair_smem<T, D>(W) : 0;
+    const size_t sm = pair_smem<T, D>(W, MODE, SOLVER, a.g.FO);
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_pair<T, D, MODE, SOLVER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(k_pair<T, D, MODE, SOLVER, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_pair<T, D, MODE, SOLVER><<<n_tiles, dim3(32, W), sm, st>>>(a);
+    k_pair<T, D, MODE, SOLVER, NR><<<n_tiles, dim3(32, W), sm, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int D, int MODE>
+cudaError_t launch_pair_m(const PairArgs<T> &a, int solver, int n_tiles, int W, cudaStream_t st) {
+    if (solver == 0) return launch_pair_t<T, D, MODE, 0, 1>(a, n_tiles, W, st);
+    if (a.g.FR <= 4) return launch_pair_t<T, D, MODE, 1, 4>(a, n_tiles, W, st);
+    if (a.g.FR <= 6) return launch_pair_t<T, D, MODE, 1, 6>(a, n_tiles, W, st);
+    return launch_pair_t<T, D, MODE, 1, 8>(a, n_tiles, W, st);
 }
 
 template <typename T>
 cudaError_t launch_pair(const PairArgs<T> &a, int dim, int mode, int solver, int n_tiles, int W, cudaStream_t st) {
-#define OCA_PAIR_CASE(D_, M_, S_) \
-    if (dim == D_ && mode == M_ && solver == S_) return launch_pair_t<T, D_, M_, S_>(a, n_tiles, W, st);
-    OCA_PAIR_CASE(2, 0, 0) OCA_PAIR_CASE(2, 0, 1) OCA_PAIR_CASE(2, 1, 0) OCA_PAIR_CASE(2, 1, 1)
-    OCA_PAIR_CASE(3, 0, 0) OCA_PAIR_CASE(3, 0, 1) OCA_PAIR_CASE(3, 1, 0) OCA_PAIR_CASE(3, 1, 1)
-#undef OCA_PAIR_CASE
+    if (dim == 2) return mode == 0 ? launch_pair_m<T, 2, 0>(a, solver, n_tiles, W, st) : launch_pair_m<T, 2, 1>(a, solver, n_tiles, W, st);
+    if (dim == 3) return mode == 0 ? launch_pair_m<T, 3, 0>(a, solver, n_tiles, W, st) : launch_pair_m<T, 3, 1>(a, solver, n_tiles, W, st);
     return cudaErrorInvalidValue;
 }
 

@@ -838,6 +838,286 @@ OCA_HD inline T ssn_value(const Lane<T, D> &L, const T *ybar, long long P, int F
 }
 
 // ============================================================================
+// Semismooth Newton with staged generator data (the form the pair kernel
+// runs).  Per pair, the robot faces live in registers and the obstacle
+// faces' body-frame offsets d'_m, proximal reciprocals 1/(rho |K_m|^2),
+// previous values ybar_m and constants rho |K_m|^2 ybar_m^2 are staged once
+// in shared memory (lane-major: element m of thread tid at [m * BT + tid]),
+// so that each evaluation of y(w) costs one pass of multiply-adds over the
+// faces with no division.  Same mathematics as ssn_eval/ssn_solve above.
+// ============================================================================
+template <typename T, int D, int NR>
+struct SsnLane {
+    // pose
+    T R[D * D];
+    // robot part
+    int nr;
+    T a[NR][D], b[NR];
+    T iDr[NR];   // 1 / (rho |a_k|^2)
+    T Db[NR];    // |a_k|^2 / b_k        (breakpoint scale)
+    T bD[NR];    // b_k / |a_k|^2
+    T b2D[NR];   // b_k^2 / |a_k|^2
+    T rD[NR];    // rho |a_k|^2
+    T iD[NR];    // 1 / |a_k|^2
+    T yl[NR];    // previous lambda
+    // obstacle faces (shared memory) and world normals (global)
+    int no;
+    const T *C;          // [no][D] world normals
+    const T *sdp, *siD, *syb, *sq;  // [m * BT] + tid
+    int BT;
+    // slack
+    T ybg;
+};
+
+template <typename T, int D, int NR>
+struct SsnEval {
+    T lam[NR];
+    T Kty[D + 1];
+    T psi, pmag, mag;
+    T H[D + 1][D + 1];
+};
+
+template <typename T, int D, int NR>
+OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, const T bq[D + 1], const T w[D + 1],
+                                   SsnEval<T, D, NR> &st) {
+    constexpr int V = D + 1;
+    // lambda: z_k = ybar_k - a_k.w1 / (rho |a_k|^2), breakpoints t_k = z_k |a_k|^2 / b_k
+    T z[NR], t[NR], h[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        T hk = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) hk += L.a[k][i] * w[1 + i];
+        h[k] = hk;
+        z[k] = L.yl[k] - hk * L.iDr[k];
+        t[k] = k < L.nr ? z[k] * L.Db[k] : T(-3.0e38);
+    }
+    // threshold tau: on the active set {t_j >= tau}, sum b z - tau sum b^2/D = 1;
+    // the active set is the largest {t_j >= t_k} whose tau stays below t_k
+    T tau = T(0);
+    int best_n = -1;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        T s1 = T(0), s2 = T(0);
+        int n = 0;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j < L.nr && t[j] >= t[k]) {
+                s1 += L.b[j] * z[j];
+                s2 += L.b2D[j];
+                ++n;
+            }
+        }
+        const T tc = (s1 - T(1)) / s2;
+        if (k < L.nr && tc < t[k] && n > best_n) {
+            best_n = n;
+            tau = tc;
+        }
+    }
+    T half_pen = T(0), lin = T(0), lmag = T(0), mag = T(0);
+    T a1[D], sc[D], sd = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        a1[i] = T(0);
+        sc[i] = T(0);
+    }
+    T Ha[D][D], ba[D], bb = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        ba[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) Ha[i][j] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const T lk = k < L.nr ? fmax(T(0), z[k] - tau * L.bD[k]) : T(0);
+        st.lam[k] = lk;
+        if (k < L.nr) {
+            const T dl = lk - L.yl[k];
+            half_pen += T(0.5) * L.rD[k] * dl * dl;
+            lin += h[k] * lk;
+            lmag += m_abs(h[k] * lk);
+            mag += lk;
+#pragma unroll
+            for (int i = 0; i < D; ++i) a1[i] += lk * L.a[k][i];
+            if (lk > T(0)) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    ba[i] += L.b[k] * L.a[k][i] * L.iD[k];
+#pragma unroll
+                    for (int j = 0; j < D; ++j) Ha[i][j] += L.a[k][i] * L.a[k][j] * L.iD[k];
+                }
+                bb += L.b2D[k];
+            }
+        }
+    }
+    // faces: h_m = w0 d'_m + c_m.(R w1), mu_m = max(0, ybar_m - h_m / (rho |K_m|^2))
+    T Rw[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += L.R[i * D + k] * w[1 + k];
+        Rw[i] = acc;
+    }
+    // M' = sum_active [d'; c][d'; c]^T / |K_m|^2 (lifted with diag(1, R^T) afterwards)
+    T Mp[V][V];
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+#pragma unroll
+        for (int j = 0; j < V; ++j) Mp[i][j] = T(0);
+    for (int m = 0; m < L.no; ++m) {
+        const int o = m * L.BT;
+        const T dp = L.sdp[o], iDm = L.siD[o], yb = L.syb[o];
+        T c[D], cw = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            c[i] = ldg(L.C + m * D + i);
+            cw += c[i] * Rw[i];
+        }
+        const T hm = w[0] * dp + cw;
+        const T mu = fmax(T(0), yb - hm * iDm);
+        if (mu > T(0)) {
+            half_pen += T(0.5) * hm * hm * iDm;   // 0.5 rho |K|^2 (mu - ybar)^2 with mu - ybar = -h iD
+            const T wgt = rho_p * iDm;             // 1 / |K_m|^2
+            T e[V];
+            e[0] = dp;
+#pragma unroll
+            for (int i = 0; i < D; ++i) e[1 + i] = c[i];
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+#pragma unroll
+                for (int j = 0; j <= i; ++j) Mp[i][j] += wgt * e[i] * e[j];
+        } else {
+            half_pen += T(0.5) * L.sq[o];          // 0.5 rho |K|^2 ybar^2
+        }
+        lin += hm * mu;
+        lmag += (m_abs(w[0] * dp) + m_abs(cw)) * mu;
+        sd += mu * dp;
+#pragma unroll
+        for (int i = 0; i < D; ++i) sc[i] += mu * c[i];
+        mag += mu * (m_abs(dp) + T(1));
+    }
+    const T gam = fmax(T(0), L.ybg - w[0] / rho_p);
+    {
+        const T dg = gam - L.ybg;
+        half_pen += T(0.5) * rho_p * dg * dg;
+    }
+    lin += w[0] * gam;
+    mag += gam;
+    st.Kty[0] = sd + gam;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T acc = a1[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * sc[k];
+        st.Kty[1 + i] = acc;
+    }
+    T ww = T(0), bw = T(0);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        ww += w[i] * w[i];
+        bw += bq[i] * w[i];
+    }
+    st.psi = T(0.5) * ww - bw - (half_pen + lin);
+    st.mag = mag;
+    st.pmag = T(0.5) * ww + m_abs(bw) + half_pen + lmag + m_abs(w[0] * gam);
+    // H = rho I + diag(1, R^T) M' diag(1, R) + e0 e0^T [gamma active] + lambda part
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+#pragma unroll
+        for (int j = i + 1; j < V; ++j) Mp[i][j] = Mp[j][i];
+    st.H[0][0] = rho_p + Mp[0][0] + (gam > T(0) ? T(1) : T(0));
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * Mp[1 + k][0];
+        st.H[1 + i][0] = st.H[0][1 + i] = acc;
+    }
+    const T ibb = bb > T(0) ? T(1) / bb : T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T acc = (i == j) ? rho_p : T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int l = 0; l < D; ++l) acc += L.R[k * D + i] * Mp[1 + k][1 + l] * L.R[l * D + j];
+            st.H[1 + i][1 + j] = acc + Ha[i][j] - ba[i] * ba[j] * ibb;
+        }
+}
+
+template <typename T, int D, int NR>
+OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T bq[D + 1], T w[D + 1],
+                                   SsnEval<T, D, NR> &st) {
+    constexpr int V = D + 1;
+    ssn_eval_staged<T, D, NR>(L, rho_p, bq, w, st);
+    int status = OCA_PAIR_ITER_CAP;
+    for (int it = 0; it < 60; ++it) {
+        T F[V], fn = T(0), scale = T(1) + st.mag;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            F[i] = w[i] - bq[i] - st.Kty[i];
+            fn = fmax(fn, m_abs(F[i]));
+            scale = fmax(scale, fmax(m_abs(w[i]), m_abs(bq[i])));
+        }
+        if (fn <= T(16) * m_eps<T>() * scale) {
+            status = OCA_PAIR_OK;
+            break;
+        }
+        if (!(fn == fn)) {
+            status = OCA_PAIR_NONFINITE;
+            break;
+        }
+        T G[V][V], dlt[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            dlt[i] = -rho_p * F[i];
+#pragma unroll
+            for (int j = 0; j < V; ++j) G[i][j] = st.H[i][j];
+        }
+        if (!chol_solve<T, V>(G, dlt, V, T(0))) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) dlt[i] = -F[i];
+        }
+        T gd = T(0);
+#pragma unroll
+        for (int i = 0; i < V; ++i) gd += F[i] * dlt[i];
+        if (!(gd < T(0))) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) dlt[i] = -F[i];
+            gd = T(0);
+#pragma unroll
+            for (int i = 0; i < V; ++i) gd -= F[i] * F[i];
+        }
+        T tstep = T(1);
+        SsnEval<T, D, NR> trial;
+        T wt[V];
+        bool ok = false;
+        for (int ls = 0; ls < 30; ++ls) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) wt[i] = w[i] + tstep * dlt[i];
+            ssn_eval_staged<T, D, NR>(L, rho_p, bq, wt, trial);
+            if (trial.psi <= st.psi + T(1e-4) * tstep * gd + T(8) * m_eps<T>() * (st.pmag + trial.pmag)) {
+                ok = true;
+                break;
+            }
+            tstep *= T(0.5);
+        }
+#pragma unroll
+        for (int i = 0; i < V; ++i) w[i] = wt[i];
+        st = trial;
+        if (!ok) {
+            status = OCA_PAIR_OK;  // no decrease at rounding level
+            break;
+        }
+    }
+    return status;
+}
+
+// ============================================================================
 // Scale LP (Sec. III-A eqn:scale_opt) through its dual (eqn:scale_opt_dual):
 //   min d'^T mu  s.t.  b^T lambda = 1,  A^T lambda + C'^T mu = 0,  lambda, mu >= 0
 // by a revised two-phase simplex with Bland's rule on D+1 equality rows.
