@@ -239,6 +239,31 @@ oca_status oca_admm_solve(oca_ctx *ctx, const oca_scene *scene, const oca_model 
                           void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Collision detection without allocation                                   */
+/* ------------------------------------------------------------------------ */
+
+/* The same results as oca_scale_detect_batch (alpha*, optional lambda*, mu*,
+ * verdict, status; no certificate margin) for a scene of exactly one
+ * scenario, without creating an oca_scene and without allocating anything,
+ * on the device or the host.  For callers that cannot allocate: a real-time
+ * control loop that must stay out of the CUDA allocator (which can block or
+ * synchronise), or code under a host that forbids heap use.  The paper has
+ * no counterpart of this entry point.
+ * desc: as for oca_scene_create with n_scen == 1 (host metadata, device
+ * geometry); the face counts and part links are copied into a file-scope
+ * device scratch array of 1 MiB that also holds the poses, so
+ * 4 * (M + 2 * n_parts) (rounded up to 256) + (dim + dim^2) * n_parts * N *
+ * sizeof(element) must not exceed 1 MiB, else OCA_ERR_CAPACITY; other argument
+ * errors give OCA_ERR_INVALID_ARGUMENT before any work is queued.
+ * Every GPU that loads the library holds the 1 MiB until the process exits.
+ * The first call on a device looks up the array's device address (make that
+ * call before any stream capture); all calls on a device share the array, so
+ * calls whose work overlaps on the GPU race. */
+oca_status oca_scale_detect_noalloc(const oca_scene_desc *desc, const oca_model *model, const void *states,
+                                    void *alpha, void *lambda, void *mu, int32_t *verdict, int32_t *status,
+                                    void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Kernel timing                                                            */
 /* ------------------------------------------------------------------------ */
 typedef struct {

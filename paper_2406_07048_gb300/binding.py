@@ -69,7 +69,8 @@ class Report(C.Structure):
 
 EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create", "oca_scene_destroy",
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
-            "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read"]
+            "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
+            "oca_scale_detect_noalloc"]
 
 
 def lib():
@@ -107,6 +108,8 @@ def lib():
         L.oca_profile_enable.restype = I
         L.oca_profile_read.argtypes = [P, C.POINTER(ProfileStats)]
         L.oca_profile_read.restype = I
+        L.oca_scale_detect_noalloc.argtypes = [C.POINTER(SceneDesc), C.POINTER(ModelC), P, P, P, P, P, P, P]
+        L.oca_scale_detect_noalloc.restype = I
         _lib = L
     return _lib
 
@@ -257,6 +260,21 @@ def scale_detect(ds: DeviceScene, states: torch.Tensor, want_certificate: bool =
                                         _ptr(mu), _ptr(margin), _ptr(verdict), _ptr(status), _stream(stream)),
            "oca_scale_detect_batch")
     return dict(alpha=alpha, lam=lam, mu=mu, margin=margin, verdict=verdict, status=status)
+
+
+def scale_detect_noalloc(ds: DeviceScene, states: torch.Tensor, want_certificate: bool = True, stream=None):
+    """oca_scale_detect_noalloc on a one-scenario scene (the library allocates
+    nothing; the output tensors are allocated here by PyTorch)."""
+    P = ds.n_pairs
+    alpha = torch.empty(P, dtype=ds.dtype, device=ds.device)
+    lam = torch.zeros(ds.scene.fr_max, P, dtype=ds.dtype, device=ds.device) if want_certificate else None
+    mu = torch.zeros(ds.scene.fo_max, P, dtype=ds.dtype, device=ds.device) if want_certificate else None
+    verdict = torch.empty(P, dtype=torch.int32, device=ds.device)
+    status = torch.empty(P, dtype=torch.int32, device=ds.device)
+    _check(lib().oca_scale_detect_noalloc(C.byref(ds.desc), C.byref(ds.model), _ptr(states), _ptr(alpha), _ptr(lam),
+                                          _ptr(mu), _ptr(verdict), _ptr(status), _stream(stream)),
+           "oca_scale_detect_noalloc")
+    return dict(alpha=alpha, lam=lam, mu=mu, verdict=verdict, status=status)
 
 
 def pair_qp(ds: DeviceScene, states, zeta, xi, y_in, prox: float = 0.0, y_out=None, want_v=True, stream=None):
