@@ -139,7 +139,7 @@ def gpu_arm(args):
 
     # --- autotune the warps per tile on the step-1 kernel at the initial state
     tune = {}
-    for w in (1, 2, 4, 8, 16):
+    for w in ((1, 2, 4, 8, 16) if args.warps <= 0 else ()):
         ds.warps = w
         for _ in range(2):
             binding.pair_qp(ds, pb.s, pb.zeta, pb.xi, y0, prox=params["prox"], y_out=pb.y, want_v=False)
@@ -151,7 +151,7 @@ def gpu_arm(args):
         e1.record()
         torch.cuda.synchronize()
         tune[w] = e0.elapsed_time(e1) / 3
-    best_w = min(tune, key=tune.get)
+    best_w = min(tune, key=tune.get) if tune else args.warps
     ds.warps = best_w
 
     stream = torch.cuda.current_stream()
@@ -196,7 +196,7 @@ def gpu_arm(args):
         dist.barrier()
     clk = clocks.stop()
 
-    qp_solves, converged, algo_bytes = 0.0, 0, 0.0
+    qp_solves, converged, algo_bytes, pair_units = 0.0, 0, 0.0, 0.0
     iters_all = []
     d1 = scene.dim + 1
     ny_sum = (bpp / 4 - 2 * d1 * pc) / 2               # sum over a scenario's pairs of n_y
@@ -214,8 +214,9 @@ def gpu_arm(args):
         capped = st == 1
         n_full = np.where(capped, np.maximum(it - 1, 0), it)
         algo_bytes += float((b_first + n_full * b_full + capped * b_head).sum())
-    tot = np.array([qp_solves, converged, ms, algo_bytes, prof["pair_ms"], prof["traj_ms"], prof["pair_launches"]],
-                   dtype=np.float64)
+        pair_units += float((pc * (it + 1)).sum())
+    tot = np.array([qp_solves, converged, ms, algo_bytes, prof["pair_ms"], prof["traj_ms"], prof["pair_launches"],
+                    pair_units], dtype=np.float64)
     if dist:
         t = torch.tensor(tot, device=dev)
         tmax = t.clone()
@@ -277,12 +278,17 @@ def gpu_arm(args):
     peak, peak_kind = _peaks()
     achieved = tot[3] / (tot[4] / 1e3) / 1e9 if tot[4] > 0 else 0.0
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "k_pair_traffic.json")
+    tp = os.path.join(ROOT, "profiles", "k_pair_traffic.txt")
     if os.path.exists(tp):
+        kv = {}
         with open(tp) as f:
-            tj = json.load(f)
-        if tj.get("kernel_sha") == _kernel_sha():
-            traffic = tj.get("bytes_per_launch_full_workload")
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    kv[k] = v
+        if kv.get("kernel_sha") == _kernel_sha() and tot[6] > 0:
+            # measured DRAM bytes per pair, scaled to the pairs an average launch processed
+            traffic = float(kv["dram_bytes_per_pair"]) * tot[7] / tot[6]
     # per step: reset, 2 box inits, poses, gather, scale-detect poses + LP = 7,
     # and per iteration launch: pair kernel, trajectory kernel, counter advance
     launches = int(7 * args.steps * world + 3 * tot[6])
@@ -406,6 +412,7 @@ def main():
     ap.add_argument("--plain", type=int, default=16, help="scenarios timed in the plain per-scenario form")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--warps", type=int, default=0, help="warps per tile (0: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -1092,6 +1092,9 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
 #pragma unroll
             for (int i = 0; i < V; ++i) gd -= F[i] * F[i];
         }
+        // backtracking on psi: psi is piecewise quadratic along the ray, so the
+        // minimiser of the quadratic through psi(0), psi'(0) = gd and psi(t)
+        // is usually exact after one rejected trial
         T tstep = T(1);
         SsnEval<T, D, NR> trial;
         T wt[V];
@@ -1104,7 +1107,9 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
                 ok = true;
                 break;
             }
-            tstep *= T(0.5);
+            const T curv = trial.psi - st.psi - tstep * gd;   // (psi(t) - psi(0) - t psi'(0)) = a t^2
+            T tn = curv > T(0) ? -gd * tstep * tstep / (T(2) * curv) : T(0.5) * tstep;
+            tstep = fmin(fmax(tn, T(0.1) * tstep), T(0.5) * tstep);
         }
 #pragma unroll
         for (int i = 0; i < V; ++i) w[i] = wt[i];
