@@ -136,6 +136,8 @@ def gpu_arm(args):
     s0, u0, y0 = pb.s.clone(), pb.u.clone(), pb.y.clone()
     params = dict(binding.DEFAULTS)
     params["max_iter"] = args.max_iter
+    if args.riccati_f32:
+        params["flags"] = binding.OCA_ADMM_RICCATI_F32
 
     # --- autotune the warps per tile on the step-1 kernel at the initial state
     tune = {}
@@ -301,7 +303,8 @@ def gpu_arm(args):
                                f"obstacles~U[8,64], 3-16 faces, 1-2 parts), cold start, max_iter {args.max_iter}",
                    "scenarios_per_gpu": S, "pairs_per_gpu": int(scene.n_pairs),
                    "admm": {k: params[k] for k in ("sigma", "eps_pri", "eps_dual", "prox", "rho_box", "damp")},
-                   "precision": "pair QPs / residuals / duals FP32, Riccati factorisation FP64",
+                   "precision": "pair QPs / residuals / duals FP32, Riccati factorisation "
+                                + ("FP32" if args.riccati_f32 else "FP64"),
                    "warps_per_tile": best_w, "tuner_ms": {str(k): round(v, 4) for k, v in tune.items()},
                    "l2": "inputs larger than L2 (y alone %.0f MB)" % (pb.y.numel() * 4 / 1e6),
                    "parallelism": f"scenario shards x{world}"},
@@ -413,6 +416,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warps", type=int, default=0, help="warps per tile (0: autotune)")
+    ap.add_argument("--riccati-f32", action="store_true", help="factorise the trajectory QP in FP32")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

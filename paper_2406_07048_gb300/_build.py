@@ -28,11 +28,16 @@ def nvcc() -> str:
 def _stale(target: str, deps) -> bool:
     if not os.path.exists(target):
         return True
+    stamp = target + ".flags"
+    flags = os.environ.get("OCA_NVCC_EXTRA", "")
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        return True
     t = os.path.getmtime(target)
     return any(os.path.getmtime(d) > t for d in deps)
 
 
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+    extra = list(extra or []) + [f for f in os.environ.get("OCA_NVCC_EXTRA", "").split() if f]
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "oca.h"))
@@ -43,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc()] + ARCH + FLAGS + (extra or []) + ["-c", s, "-o", o]
+            cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", s, "-o", o]
             jobs.append(cmd)
 
     def run(cmd):
@@ -56,6 +61,9 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
+    for o in objs:
+        with open(o + ".flags", "w") as fh:
+            fh.write(os.environ.get("OCA_NVCC_EXTRA", ""))
     if force or jobs or _stale(LIB, objs):
         run([nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs)
         os.replace(LIB + ".tmp", LIB)

@@ -57,8 +57,14 @@ __global__ void k_pose(PoseArgs<T> a) {
 //                    w = C^T mu, c = 1 + d^T mu + gamma + zeta, e = A^T lambda + xi
 //     y buffers alternate by the parity of j (y_in = buf[j%2], y_out = buf[(j+1)%2]).
 // ============================================================================
+#ifndef OCA_PAIR_MIN_BLOCKS
+#define OCA_PAIR_MIN_BLOCKS 1
+#endif
+#ifndef OCA_PAIR_MAX_THREADS
+#define OCA_PAIR_MAX_THREADS 512
+#endif
 template <typename T, int D, int MODE, int SOLVER, int NR>
-__global__ void __launch_bounds__(512) k_pair(PairArgs<T> a) {
+__global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_pair(PairArgs<T> a) {
     constexpr int V = D + 1, SM = D + 2, NSTAT = StatDims<D>::NSTAT, NW = StatDims<D>::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Tile tile = a.tiles[blockIdx.x];

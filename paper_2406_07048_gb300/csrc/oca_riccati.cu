@@ -123,95 +123,98 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
     for (int i = 0; i < 12; ++i) mdl.Qs[i] = F(a.model.Qs[i]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) mdl.Qu[i] = F(a.model.Qu[i]);
-    const F sigma = F(a.sigma), rho_b = F(a.rho_box), damp = F(a.damp);
+    const F rho_b = F(a.rho_box), damp = F(a.damp);
     F *scr = reinterpret_cast<F *>(a.scratch) + a.scratch0[s];
 
     // ---- 2. stage assembly, lanes over t
+    // (in the array precision T: only the factorisation below runs in F)
+    const DevModel<T> &mdt = a.model;
     for (int t = lane; t <= N; t += 32) {
-        F st[NS];
+        T st[NS];
 #pragma unroll
-        for (int i = 0; i < NS; ++i) st[i] = F(a.s[(long long)(sm.state0 + t) * NS + i]);
+        for (int i = 0; i < NS; ++i) st[i] = a.s[(long long)(sm.state0 + t) * NS + i];
         if (t < N) {
-            F ut[NU], f[NS], fs[NS * NS], fu[NS * NU];
+            T ut[NU], f[NS], fs[NS * NS], fu[NS * NU];
 #pragma unroll
-            for (int i = 0; i < NU; ++i) ut[i] = F(a.u[(long long)(sm.ctrl0 + t) * NU + i]);
-            dynamics<F, KIND>(mdl, st, ut, f, fs, fu);
+            for (int i = 0; i < NU; ++i) ut[i] = a.u[(long long)(sm.ctrl0 + t) * NU + i];
+            dynamics<T, KIND>(mdt, st, ut, f, fs, fu);
             F *At = scr + LY::A(N, t), *Bt = scr + LY::B(N, t), *ct = scr + LY::c(N, t);
             for (int i = 0; i < NS; ++i) {
-                F acc = st[i] + mdl.dt * f[i];
+                T acc = st[i] + mdt.dt * f[i];
                 for (int k = 0; k < NS; ++k) {
-                    const F v = (i == k ? F(1) : F(0)) + mdl.dt * fs[i * NS + k];
-                    At[i * NS + k] = v;
+                    const T v = (i == k ? T(1) : T(0)) + mdt.dt * fs[i * NS + k];
+                    At[i * NS + k] = F(v);
                     acc -= v * st[k];
                 }
                 for (int k = 0; k < NU; ++k) {
-                    const F v = mdl.dt * fu[i * NU + k];
-                    Bt[i * NU + k] = v;
-                    acc -= v * F(a.u[(long long)(sm.ctrl0 + t) * NU + k]);
+                    const T v = mdt.dt * fu[i * NU + k];
+                    Bt[i * NU + k] = F(v);
+                    acc -= v * ut[k];
                 }
-                ct[i] = acc;
+                ct[i] = F(acc);
             }
         }
-        F *Qt = scr + LY::Q(N, t), *qt = scr + LY::q(N, t);
-        for (int i = 0; i < NS * NS; ++i) Qt[i] = F(0);
+        // stage cost accumulated in registers (T), stored once in F
+        T Qr[NS * NS], qr[NS];
+        for (int i = 0; i < NS * NS; ++i) Qr[i] = T(0);
         for (int i = 0; i < NS; ++i) {
-            Qt[i * NS + i] = F(2) * mdl.Qs[i];
-            qt[i] = -F(2) * mdl.Qs[i] * F(a.s_ref[(long long)(sm.state0 + t) * NS + i]);
+            Qr[i * NS + i] = T(2) * mdt.Qs[i];
+            qr[i] = -T(2) * mdt.Qs[i] * a.s_ref[(long long)(sm.state0 + t) * NS + i];
             if (t >= 1) {
                 // proximal damping 0.5 damp |s - s^j|^2 and the box block's
                 // augmented term 0.5 rho_b |s - z + w|^2 on bounded components
-                Qt[i * NS + i] += damp;
-                qt[i] -= damp * st[i];
+                Qr[i * NS + i] += a.damp;
+                qr[i] -= a.damp * st[i];
                 if (bounded(a.model.s_lo[i], a.model.s_hi[i])) {
                     const long long k2 = (long long)(sm.state0 + t) * NS + i;
-                    Qt[i * NS + i] += rho_b;
-                    qt[i] -= rho_b * (F(a.box_zs[k2]) - F(a.box_ws[k2]));
+                    Qr[i * NS + i] += a.rho_box;
+                    qr[i] -= a.rho_box * (a.box_zs[k2] - a.box_ws[k2]);
                 }
             }
         }
         if (t >= 1) {
             for (int part = 0; part < sm.NP; ++part) {
                 const int gp = sm.part0 + part;
-                F off[D], rho[D], R[D * D], drho[D * NS], dR[NROT][D * D];
+                T off[D], rho[D], R[D * D], drho[D * NS], dR[NROT][D * D];
                 int ridx[NROT];
 #pragma unroll
-                for (int i = 0; i < D; ++i) off[i] = F(a.g.part_off[gp * D + i]);
-                part_pose<F, KIND>(mdl, a.g.part_link[gp], off, st, rho, R, drho, dR, ridx);
+                for (int i = 0; i < D; ++i) off[i] = a.g.part_off[gp * D + i];
+                part_pose<T, KIND>(mdt, a.g.part_link[gp], off, st, rho, R, drho, dR, ridx);
                 const long long col = sm.qbeg + part * N + (t - 1);
-                F W[D][D], Wc[D], E[D][D];
+                T W[D][D], Wc[D], E[D][D];
                 int k = 0;
 #pragma unroll
                 for (int i = 0; i < D; ++i)
 #pragma unroll
                     for (int jj = 0; jj <= i; ++jj) {
-                        W[i][jj] = W[jj][i] = F(a.stats[(long long)k * a.Qtot + col]);
+                        W[i][jj] = W[jj][i] = a.stats[(long long)k * a.Qtot + col];
                         ++k;
                     }
 #pragma unroll
-                for (int i = 0; i < D; ++i) Wc[i] = F(a.stats[(long long)(NW + i) * a.Qtot + col]);
+                for (int i = 0; i < D; ++i) Wc[i] = a.stats[(long long)(NW + i) * a.Qtot + col];
 #pragma unroll
                 for (int i = 0; i < D; ++i)
 #pragma unroll
-                    for (int jj = 0; jj < D; ++jj) E[i][jj] = F(a.stats[(long long)(NW + D + i * D + jj) * a.Qtot + col]);
+                    for (int jj = 0; jj < D; ++jj) E[i][jj] = a.stats[(long long)(NW + D + i * D + jj) * a.Qtot + col];
                 // translation block: drho^T W drho, gradient -drho^T (Wc - W rho)
-                F WD[D][NS], gvec[D];
+                T WD[D][NS], gvec[D];
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    F acc = Wc[i];
+                    T acc = Wc[i];
 #pragma unroll
                     for (int jj = 0; jj < D; ++jj) acc -= W[i][jj] * rho[jj];
                     gvec[i] = acc;
                     for (int b2 = 0; b2 < NS; ++b2) {
-                        F v = F(0);
+                        T v = T(0);
 #pragma unroll
                         for (int jj = 0; jj < D; ++jj) v += W[i][jj] * drho[jj * NS + b2];
                         WD[i][b2] = v;
                     }
                 }
-                F Hs[NS], gs = F(0);
+                T Hs[NS];
                 for (int a2 = 0; a2 < NS; ++a2) {
                     for (int b2 = 0; b2 < NS; ++b2) {
-                        F v = F(0);
+                        T v = T(0);
 #pragma unroll
                         for (int i = 0; i < D; ++i) v += drho[i * NS + a2] * WD[i][b2];
                         Hs[b2] = v;
@@ -222,12 +225,12 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
                         if (ridx[ra] != a2) continue;
 #pragma unroll
                         for (int rb = 0; rb < NROT; ++rb) {
-                            F v = F(0);
+                            T v = T(0);
 #pragma unroll
                             for (int i = 0; i < D; ++i)
 #pragma unroll
                                 for (int jj = 0; jj < D; ++jj) {
-                                    F m = F(0);
+                                    T m = T(0);
 #pragma unroll
                                     for (int l = 0; l < D; ++l) m += dR[ra][i * D + l] * dR[rb][jj * D + l];
                                     v += m * W[i][jj];
@@ -235,33 +238,36 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
                             Hs[ridx[rb]] += v;
                         }
                     }
-                    F g = F(0);
+                    T g = T(0);
 #pragma unroll
                     for (int i = 0; i < D; ++i) g -= drho[i * NS + a2] * gvec[i];
 #pragma unroll
                     for (int ra = 0; ra < NROT; ++ra) {
                         if (ridx[ra] != a2) continue;
-                        F v = F(0);
+                        T v = T(0);
 #pragma unroll
                         for (int i = 0; i < D; ++i)
 #pragma unroll
                             for (int jj = 0; jj < D; ++jj) {
-                                F m = F(0);
+                                T m = T(0);
 #pragma unroll
                                 for (int l = 0; l < D; ++l) m += dR[ra][i * D + l] * R[jj * D + l];
                                 v += dR[ra][i * D + jj] * E[i][jj] + m * W[i][jj];
                             }
                         g += v;
                     }
-                    F hsx = F(0);
+                    T hsx = T(0);
                     for (int b2 = 0; b2 < NS; ++b2) {
-                        Qt[a2 * NS + b2] += sigma * Hs[b2];
+                        Qr[a2 * NS + b2] += a.sigma * Hs[b2];
                         hsx += Hs[b2] * st[b2];
                     }
-                    qt[a2] += sigma * (g - hsx);
+                    qr[a2] += a.sigma * (g - hsx);
                 }
             }
         }
+        F *Qt = scr + LY::Q(N, t), *qt = scr + LY::q(N, t);
+        for (int i = 0; i < NS * NS; ++i) Qt[i] = F(Qr[i]);
+        for (int i = 0; i < NS; ++i) qt[i] = F(qr[i]);
     }
     __syncwarp();
 
