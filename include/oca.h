@@ -239,6 +239,55 @@ oca_status oca_admm_solve(oca_ctx *ctx, const oca_scene *scene, const oca_model 
                           void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Differentiation: adjoint of the unrolled ADMM                            */
+/* ------------------------------------------------------------------------ */
+/* The paper solves the MPC problem and stops there; these three calls add a
+ * reverse-mode gradient of the solution with respect to the obstacles.
+ * A taped solve records every iterate (s^k, u^k, y^k, zeta^k, xi^k, the box
+ * block and the Gauss-Newton statistics) so that oca_admm_backward can run
+ * the iterations of Sec. IV-B backwards: per pair it differentiates the pair
+ * QP through its optimality conditions on the active set (implicit function
+ * theorem; prox > 0 makes the QP strictly convex and its solution unique),
+ * per scenario it solves the adjoint of each trajectory LQ with the same
+ * Riccati factorisation (FP64) and differentiates the linearisation point
+ * through the second derivatives of the dynamics and of the part poses.
+ * The result is the exact derivative of the map the solve executed (its
+ * iteration count held fixed); it is defined where no pair's active set
+ * changes, i.e. at strictly complementary pair solutions. */
+
+/* Size in bytes of the tape for this scene, model and iteration cap: the
+ * iterates of a solve with max_iter iterations and the backward pass's work
+ * area.  About (max_iter + 1) * (ny_max + dim + 1) * n_pairs elements.
+ * Errors: OCA_ERR_INVALID_ARGUMENT. */
+oca_status oca_admm_tape_bytes(const oca_scene *scene, const oca_model *model, int32_t max_iter, int64_t *bytes);
+/* oca_admm_solve that also records its iterates in `tape` (caller-owned
+ * device memory, 256-byte aligned, tape_bytes >= oca_admm_tape_bytes(...,
+ * params->max_iter); else OCA_ERR_INVALID_ARGUMENT / OCA_ERR_CAPACITY).
+ * Same results as oca_admm_solve; runs without iteration graphs. */
+oca_status oca_admm_solve_taped(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                                const oca_admm_params *params, const void *s_ref, void *s, void *u, void *y,
+                                void *zeta, void *xi, const oca_admm_report *report, void *tape, int64_t tape_bytes,
+                                void *stream);
+/* Gradient of L = sum_s grad_cost[s] * F_s, F_s the trajectory cost of
+ * eqn:navigation_cost returned by the taped solve for scenario s, with
+ * respect to the obstacle offsets d, the obstacle translations and the
+ * initial states.  Arguments: the scene, model, params and s_ref of the
+ * taped solve; tape, tape_bytes as given to it (its work area is
+ * overwritten); iters = report.iters of that solve (device, [S]);
+ * grad_cost [S] (device, scene dtype).
+ * Outputs (device, scene dtype, each may be NULL but not all three):
+ *   grad_obs_offset [M_tot][fo_max]  dL/dd_m (pad faces 0);
+ *   grad_obs_center [M_tot][dim]     dL/ddelta for a translation delta of the
+ *                                    obstacle (offsets d_m + c_m . delta);
+ *   grad_state0     [S][ns]          dL/ds_0.
+ * grad_alpha must be NULL (per-pair alpha* gradients are not part of this
+ * build: OCA_ERR_UNSUPPORTED); prox must be > 0 (OCA_ERR_UNSUPPORTED).
+ * Scenarios whose solve FAILED get meaningless gradients. */
+oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                             const oca_admm_params *params, const void *s_ref, void *tape, int64_t tape_bytes,
+                             const int32_t *iters, const void *grad_cost, const void *grad_alpha,
+                             void *grad_obs_offset, void *grad_obs_center, void *grad_state0, void *stream);
+/* ------------------------------------------------------------------------ */
 /* Collision detection without allocation                                   */
 /* ------------------------------------------------------------------------ */
 

@@ -70,7 +70,7 @@ class Report(C.Structure):
 EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create", "oca_scene_destroy",
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
             "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
-            "oca_scale_detect_noalloc"]
+            "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward"]
 
 
 def lib():
@@ -110,6 +110,14 @@ def lib():
         L.oca_profile_read.restype = I
         L.oca_scale_detect_noalloc.argtypes = [C.POINTER(SceneDesc), C.POINTER(ModelC), P, P, P, P, P, P, P]
         L.oca_scale_detect_noalloc.restype = I
+        L.oca_admm_tape_bytes.argtypes = [P, C.POINTER(ModelC), I, C.POINTER(C.c_int64)]
+        L.oca_admm_tape_bytes.restype = I
+        L.oca_admm_solve_taped.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, P, P, P, P,
+                                           C.POINTER(Report), P, C.c_int64, P]
+        L.oca_admm_solve_taped.restype = I
+        L.oca_admm_backward.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, C.c_int64, P, P, P,
+                                        P, P, P, P]
+        L.oca_admm_backward.restype = I
         _lib = L
     return _lib
 
@@ -295,8 +303,9 @@ DEFAULTS = dict(sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.1, max_iter=300
 
 
 def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.1,
-               max_iter=300, flags=0, rho_box=100.0, damp=100.0, stream=None):
-    """oca_admm_solve: updates s, u, y, zeta, xi in place; returns the report."""
+               max_iter=300, flags=0, rho_box=100.0, damp=100.0, stream=None, tape=None):
+    """oca_admm_solve (oca_admm_solve_taped when `tape` is given): updates s,
+    u, y, zeta, xi in place; returns the report."""
     S = ds.scene.n_scen
     rep_t = dict(iters=torch.zeros(S, dtype=torch.int32, device=ds.device),
                  status=torch.full((S,), -1, dtype=torch.int32, device=ds.device),
@@ -307,9 +316,85 @@ def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1
                  rep_t["r_dual"].data_ptr(), rep_t["cost"].data_ptr())
     pr = AdmmParams(float(sigma), float(eps_pri), float(eps_dual), float(prox), int(max_iter), int(flags),
                     float(rho_box), float(damp))
-    _check(lib().oca_admm_solve(ds.ctx.h, ds.h, C.byref(ds.model), C.byref(pr), _ptr(s_ref), _ptr(s), _ptr(u),
-                                _ptr(y), _ptr(zeta), _ptr(xi), C.byref(rep), _stream(stream)), "oca_admm_solve")
+    if tape is None:
+        _check(lib().oca_admm_solve(ds.ctx.h, ds.h, C.byref(ds.model), C.byref(pr), _ptr(s_ref), _ptr(s), _ptr(u),
+                                    _ptr(y), _ptr(zeta), _ptr(xi), C.byref(rep), _stream(stream)), "oca_admm_solve")
+    else:
+        _check(lib().oca_admm_solve_taped(ds.ctx.h, ds.h, C.byref(ds.model), C.byref(pr), _ptr(s_ref), _ptr(s),
+                                          _ptr(u), _ptr(y), _ptr(zeta), _ptr(xi), C.byref(rep), _ptr(tape),
+                                          C.c_int64(tape.numel()), _stream(stream)), "oca_admm_solve_taped")
     return rep_t
+
+
+def tape_bytes(ds: DeviceScene, max_iter: int) -> int:
+    """oca_admm_tape_bytes."""
+    n = C.c_int64(0)
+    _check(lib().oca_admm_tape_bytes(ds.h, C.byref(ds.model), int(max_iter), C.byref(n)), "oca_admm_tape_bytes")
+    return int(n.value)
+
+
+def new_tape(ds: DeviceScene, max_iter: int) -> torch.Tensor:
+    """A device byte tensor large enough for a taped solve of max_iter iterations."""
+    return torch.empty(tape_bytes(ds, max_iter), dtype=torch.uint8, device=ds.device)
+
+
+def admm_backward(ds: DeviceScene, s_ref, tape, iters, grad_cost, sigma=300.0, prox=0.1, max_iter=300,
+                  rho_box=100.0, damp=100.0, eps_pri=1e-4, eps_dual=1e-4, flags=0, stream=None):
+    """oca_admm_backward: gradients of sum_s grad_cost[s] * cost_s of a taped
+    solve w.r.t. obstacle offsets [M_tot, fo_max], obstacle translations
+    [M_tot, dim] and initial states [S, ns]."""
+    sc = ds.scene
+    m_tot = int(sc.obs_begin[-1])
+    g_d = torch.zeros(m_tot, sc.fo_max, dtype=ds.dtype, device=ds.device)
+    g_c = torch.zeros(m_tot, sc.dim, dtype=ds.dtype, device=ds.device)
+    g_s0 = torch.zeros(sc.n_scen, sc.model.ns, dtype=ds.dtype, device=ds.device)
+    pr = AdmmParams(float(sigma), float(eps_pri), float(eps_dual), float(prox), int(max_iter), int(flags),
+                    float(rho_box), float(damp))
+    gc = grad_cost.to(ds.dtype).contiguous()
+    _check(lib().oca_admm_backward(ds.ctx.h, ds.h, C.byref(ds.model), C.byref(pr), _ptr(s_ref), _ptr(tape),
+                                   C.c_int64(tape.numel()), _ptr(iters), _ptr(gc), None, _ptr(g_d), _ptr(g_c),
+                                   _ptr(g_s0), _stream(stream)), "oca_admm_backward")
+    return dict(obs_offset=g_d, obs_center=g_c, state0=g_s0)
+
+
+class AdmmCost(torch.autograd.Function):
+    """Trajectory cost per scenario (eqn:navigation_cost) after an ADMM solve,
+    as a differentiable function of the obstacle offsets d [M_tot, fo_max]
+    and translations delta [M_tot, dim] (the solved obstacle j has offsets
+    d_jm + c_jm . delta_j).  Forward: a taped oca_admm_solve from the
+    problem's current state (left unchanged); backward: oca_admm_backward."""
+
+    @staticmethod
+    def forward(ctx, obs_d, obs_shift, problem, kw):
+        ds = problem.ds
+        with torch.no_grad():
+            d_eff = obs_d + torch.einsum("jmi,ji->jm", ds.obs_C.view(obs_d.shape[0], obs_d.shape[1], -1), obs_shift)
+            saved_d = ds.obs_d.clone()
+            ds.obs_d.copy_(d_eff)
+            st = [t.clone() for t in (problem.s, problem.u, problem.y, problem.zeta, problem.xi)]
+            tape = new_tape(ds, kw.get("max_iter", 300))
+            rep = admm_solve(ds, problem.s_ref, *st, tape=tape, **kw)
+        ctx.problem, ctx.kw, ctx.tape, ctx.iters = problem, kw, tape, rep["iters"]
+        ctx.d_eff, ctx.saved_d = d_eff, saved_d
+        ds.obs_d.copy_(saved_d)
+        return rep["cost"].clone()
+
+    @staticmethod
+    def backward(ctx, grad_cost):
+        problem, kw = ctx.problem, ctx.kw
+        ds = problem.ds
+        with torch.no_grad():
+            ds.obs_d.copy_(ctx.d_eff)
+            keys = ("sigma", "prox", "max_iter", "rho_box", "damp", "eps_pri", "eps_dual", "flags")
+            g = admm_backward(ds, problem.s_ref, ctx.tape, ctx.iters, grad_cost,
+                              **{k: kw[k] for k in keys if k in kw})
+            ds.obs_d.copy_(ctx.saved_d)
+        return g["obs_offset"], g["obs_center"], None, None
+
+
+def admm_cost(problem, obs_d, obs_shift, **kw):
+    """Differentiable trajectory cost of every scenario (AdmmCost)."""
+    return AdmmCost.apply(obs_d, obs_shift, problem, kw)
 
 
 class Problem:

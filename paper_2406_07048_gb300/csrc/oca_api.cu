@@ -293,9 +293,67 @@ oca_status pairqp_impl(oca_scene *sc, const oca_model *m, const void *states, co
     return OCA_OK;
 }
 
+
+// ---- tape of a solve for the adjoint: iterates, then the backward pass's
+// work area.  Offsets in elements of the scene dtype (regions 256-byte
+// aligned); the two double accumulators come last.
+struct TapeLayout {
+    long long y, zx, st, s, u, box;                   // iterate regions
+    long long y_slot, zx_slot, st_slot, s_slot, u_slot, box_slot;
+    long long yb, zb, sb, ub, bb, stb, pb;            // adjoint work area
+    long long work_end;                               // end of the T regions
+    size_t gd_byte, gs0_byte, bytes;
+};
+
+TapeLayout tape_layout(const oca_scene *sc, int kind, int K) {
+    const int NS = kind == 0 ? 4 : kind == 1 ? 5 : 12, NU = kind == 2 ? 4 : 2;
+    const int D = sc->dim, NSTAT = D * (D + 1) / 2 + D + D * D, PK = D + D * D;
+    const long long es = (long long)dsize(sc->dtype);
+    const long long al = 256 / es;
+    auto up = [&](long long x) { return (x + al - 1) / al * al; };
+    TapeLayout L;
+    L.y_slot = up((long long)sc->ny_max * sc->P);
+    L.zx_slot = up((long long)(1 + D) * sc->P);
+    L.st_slot = up((long long)NSTAT * sc->Qtot);
+    L.s_slot = up(sc->n_states * NS);
+    L.u_slot = up(sc->n_ctrls * NU);
+    L.box_slot = up(2 * sc->n_states * NS + 2 * sc->n_ctrls * NU);
+    long long o = 0;
+    L.y = o;   o += (long long)(K + 1) * L.y_slot;
+    L.zx = o;  o += (long long)K * L.zx_slot;
+    L.st = o;  o += (long long)K * L.st_slot;
+    L.s = o;   o += (long long)(K + 1) * L.s_slot;
+    L.u = o;   o += (long long)(K + 1) * L.u_slot;
+    L.box = o; o += (long long)(K + 1) * L.box_slot;
+    L.yb = o;  o += 2 * L.y_slot;
+    L.zb = o;  o += L.zx_slot;
+    L.sb = o;  o += L.s_slot;
+    L.ub = o;  o += L.u_slot;
+    L.bb = o;  o += L.box_slot;
+    L.stb = o; o += L.st_slot;
+    L.pb = o;  o += up((long long)PK * sc->Qtot);
+    L.work_end = o;
+    size_t b = (size_t)o * (size_t)es;
+    b = (b + 255) / 256 * 256;
+    L.gd_byte = b;
+    b += sizeof(double) * (size_t)sc->M_tot * sc->FO;
+    b = (b + 255) / 256 * 256;
+    L.gs0_byte = b;
+    b += sizeof(double) * (size_t)sc->S * NS;
+    L.bytes = (b + 255) / 256 * 256;
+    return L;
+}
+
+template <typename T>
+__global__ void k_cast_d2t(const double *x, long long n, T *y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = T(x[i]);
+}
+
 template <typename T>
 oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *s,
-                     void *u, void *y, void *zeta, void *xi, const oca_admm_report *rep, cudaStream_t st) {
+                     void *u, void *y, void *zeta, void *xi, const oca_admm_report *rep, cudaStream_t st,
+                     void *tape = nullptr) {
     k_reset<<<(sc->S + 255) / 256, 256, 0, st>>>(sc->d_status, sc->S, sc->d_iter, sc->d_active);
     OCA_CK(cudaGetLastError());
     const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
@@ -327,6 +385,27 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     pa.Qtot = sc->Qtot;
     pa.scen_status = nullptr;
     OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
+
+    // tape (oca_admm_solve_taped): iterate 0 now, iterate j+1 after launch j
+    TapeLayout TL{};
+    T *tp = static_cast<T *>(tape);
+    const size_t es = sizeof(T);
+    const size_t box_s = (size_t)sc->n_states * NS, box_u = (size_t)sc->n_ctrls * NU;
+    auto tape_box = [&](int slot) -> cudaError_t {
+        T *dst = tp + TL.box + (long long)slot * TL.box_slot;
+        cudaError_t e = cudaMemcpyAsync(dst, zs, es * box_s, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + box_s, ws, es * box_s, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + 2 * box_s, zu, es * box_u, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + 2 * box_s + box_u, wu, es * box_u, cudaMemcpyDeviceToDevice, st);
+        return e;
+    };
+    if (tp) {
+        TL = tape_layout(sc, m->kind, pr->max_iter);
+        OCA_CK(cudaMemcpyAsync(tp + TL.y, y, es * sc->ny_max * (size_t)sc->P, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(tp + TL.s, s, es * box_s, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(tp + TL.u, u, es * box_u, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(tape_box(0));
+    }
 
     PairArgs<T> a = pair_args<T>(sc);
     a.zeta = static_cast<T *>(zeta);
@@ -381,28 +460,51 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     auto rec = [&](cudaEvent_t e) -> cudaError_t {
         return capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
     };
-    auto one_iter = [&](int k) -> cudaError_t {
+    auto one_iter = [&](int k, long long j) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         if (prof && (e = rec(cx->ev[0][k])) != cudaSuccess) return e;
         e = launch_pair<T>(a, sc->dim, 1, solver, sc->n_tiles, sc->W, st);
         if (e != cudaSuccess) return e;
         if (prof && (e = rec(cx->ev[1][k])) != cudaSuccess) return e;
+        const bool rec_tape = tp && j < pr->max_iter;
+        if (rec_tape) {
+            // y^{j+1} sits in the buffer launch j wrote; zeta^j, xi^j after its head
+            const T *ynew = (j & 1) ? static_cast<const T *>(y) : static_cast<const T *>(sc->d_y2);
+            e = cudaMemcpyAsync(tp + TL.y + (j + 1) * TL.y_slot, ynew, es * sc->ny_max * (size_t)sc->P,
+                                cudaMemcpyDeviceToDevice, st);
+            T *zx = tp + TL.zx + j * TL.zx_slot;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(zx, zeta, es * (size_t)sc->P, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(zx + sc->P, xi, es * sc->dim * (size_t)sc->P, cudaMemcpyDeviceToDevice, st);
+            const int nstat = sc->dim * (sc->dim + 1) / 2 + sc->dim + sc->dim * sc->dim;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(tp + TL.st + j * TL.st_slot, sc->d_stats, es * nstat * (size_t)sc->Qtot,
+                                    cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
         if (prof && (e = rec(cx->ev[2][k])) != cudaSuccess) return e;
         e = launch_riccati<T>(r, f32, st);
         if (e != cudaSuccess) return e;
         if (prof && (e = rec(cx->ev[3][k])) != cudaSuccess) return e;
+        if (rec_tape) {
+            e = cudaMemcpyAsync(tp + TL.s + (j + 1) * TL.s_slot, s, es * box_s, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(tp + TL.u + (j + 1) * TL.u_slot, u, es * box_u, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = tape_box((int)(j + 1));
+            if (e != cudaSuccess) return e;
+        }
         k_advance<<<1, 1, 0, st>>>(sc->d_iter);
         return cudaGetLastError();
     };
     const int G = 8;  // iterations per chunk between host checks
     const long long n_launch = (long long)pr->max_iter + 1;  // j = 0..max_iter
     cudaGraphExec_t exec = nullptr;
-    if (st != nullptr && n_launch > G) {
+    if (st != nullptr && n_launch > G && !tp) {
         cudaGraph_t graph = nullptr;
         OCA_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         capturing = true;
         cudaError_t ce = cudaSuccess;
-        for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = one_iter(k);
+        for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = one_iter(k, k);
         capturing = false;
         cudaError_t ee = cudaStreamEndCapture(st, &graph);
         if (ce != cudaSuccess || ee != cudaSuccess) {
@@ -420,7 +522,7 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
             if (cudaGraphLaunch(exec, st) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
         } else {
             for (int k = 0; k < G && done + k < n_launch; ++k)
-                if (one_iter(k) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
+                if (one_iter(k, done + k) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
             if (out != OCA_OK) break;
         }
         if (cudaMemcpyAsync(sc->h_active, sc->d_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -452,6 +554,113 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     k_gather<T><<<gg, 256, 0, st>>>(sc->d_meta, rep->iters, static_cast<const T *>(sc->d_y2), static_cast<T *>(y), sc->P,
                                     sc->ny_max);
     OCA_CK(cudaGetLastError());
+    return OCA_OK;
+}
+
+
+template <typename T>
+oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *tape,
+                         const int32_t *iters, const void *grad_cost, void *grad_d, void *grad_ctr, void *grad_s0,
+                         cudaStream_t st) {
+    const int K = pr->max_iter;
+    const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
+    const TapeLayout TL = tape_layout(sc, m->kind, K);
+    T *tp = static_cast<T *>(tape);
+    unsigned char *tb = static_cast<unsigned char *>(tape);
+    // zero the work area and the accumulators
+    OCA_CK(cudaMemsetAsync(tp + TL.yb, 0, TL.bytes - sizeof(T) * (size_t)TL.yb, st));
+    double *gd = reinterpret_cast<double *>(tb + TL.gd_byte);
+    double *gs0 = reinterpret_cast<double *>(tb + TL.gs0_byte);
+
+    TapeView<T> tv;
+    tv.y = tp + TL.y;
+    tv.zx = tp + TL.zx;
+    tv.stats = tp + TL.st;
+    tv.s = tp + TL.s;
+    tv.u = tp + TL.u;
+    tv.box = tp + TL.box;
+    tv.y_slot = TL.y_slot;
+    tv.zx_slot = TL.zx_slot;
+    tv.stats_slot = TL.st_slot;
+    tv.s_slot = TL.s_slot;
+    tv.u_slot = TL.u_slot;
+    tv.box_slot = TL.box_slot;
+    tv.n_states = sc->n_states;
+    tv.n_ctrls = sc->n_ctrls;
+
+    T *bb = tp + TL.bb;
+    const long long box_s = sc->n_states * NS, box_u = sc->n_ctrls * NU;
+    AdjTrajArgs<T> ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.meta = sc->d_meta;
+    ta.g = make_geom<T>(sc);
+    ta.model = make_model<T>(m);
+    ta.sigma = T(pr->sigma);
+    ta.rho_box = T(pr->rho_box);
+    ta.damp = T(pr->damp);
+    ta.s_ref = static_cast<const T *>(s_ref);
+    ta.Qtot = sc->Qtot;
+    ta.iters = iters;
+    ta.tape = tv;
+    ta.grad_cost = static_cast<const T *>(grad_cost);
+    ta.sb = tp + TL.sb;
+    ta.ub = tp + TL.ub;
+    ta.zsb = bb;
+    ta.wsb = bb + box_s;
+    ta.zub = bb + 2 * box_s;
+    ta.wub = bb + 2 * box_s + box_u;
+    ta.statsb = tp + TL.stb;
+    ta.poseb = tp + TL.pb;
+    ta.gs0 = gs0;
+    ta.scratch = sc->d_ric;
+    ta.scratch0 = sc->d_ric_off;
+    OCA_CK(launch_adj_seed<T>(ta, sc->S, st));
+
+    PoseArgs<T> pa;
+    pa.meta = sc->d_meta;
+    pa.n_scen = sc->S;
+    pa.g = make_geom<T>(sc);
+    pa.model = make_model<T>(m);
+    pa.pose = static_cast<T *>(sc->d_pose);
+    pa.Qtot = sc->Qtot;
+    pa.scen_status = nullptr;
+
+    AdjPairArgs<T> ap;
+    std::memset(&ap, 0, sizeof(ap));
+    ap.meta = sc->d_meta;
+    ap.tiles = sc->d_tiles;
+    ap.g = make_geom<T>(sc);
+    ap.pose = static_cast<const T *>(sc->d_pose);
+    ap.Qtot = sc->Qtot;
+    ap.P = sc->P;
+    ap.prox = T(pr->prox);
+    ap.iters = iters;
+    ap.zb = tp + TL.zb;
+    ap.xb = tp + TL.zb + sc->P;
+    ap.statsb = tp + TL.stb;
+    ap.poseb = tp + TL.pb;
+    ap.gd = gd;
+    const int W = std::min(sc->W, 8);
+    for (int k = K - 1; k >= 0; --k) {
+        ta.k = k;
+        OCA_CK(launch_adj_traj<T>(ta, sc->S, st));
+        pa.states = tp + TL.s + (long long)k * TL.s_slot;
+        OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
+        ap.k = k;
+        ap.y_k = tp + TL.y + (long long)k * TL.y_slot;
+        ap.y_k1 = tp + TL.y + (long long)(k + 1) * TL.y_slot;
+        ap.zx_k = tp + TL.zx + (long long)k * TL.zx_slot;
+        ap.ybar_in = tp + TL.yb + (long long)((k + 1) & 1) * TL.y_slot;
+        ap.ybar_out = tp + TL.yb + (long long)(k & 1) * TL.y_slot;
+        OCA_CK(launch_adj_pair<T>(ap, sc->dim, sc->n_tiles, W, st));
+    }
+    OCA_CK(launch_adj_finish<T>(gd, static_cast<const T *>(sc->obs_C), sc->d_obs_nf, sc->M_tot, sc->FO, sc->dim,
+                                static_cast<T *>(grad_d), static_cast<T *>(grad_ctr), st));
+    if (grad_s0) {
+        const long long n = (long long)sc->S * NS;
+        k_cast_d2t<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gs0, n, static_cast<T *>(grad_s0));
+        OCA_CK(cudaGetLastError());
+    }
     return OCA_OK;
 }
 
@@ -791,6 +1000,65 @@ oca_status oca_admm_solve(oca_ctx *ctx, const oca_scene *scene, const oca_model 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (sc->dtype == OCA_F32) return admm_impl<float>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st);
     return admm_impl<double>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st);
+}
+
+
+oca_status oca_admm_tape_bytes(const oca_scene *scene, const oca_model *model, int32_t max_iter, int64_t *bytes) {
+    if (!scene || !bytes || max_iter < 0) return OCA_ERR_INVALID_ARGUMENT;
+    oca_status e = check_model(scene, model);
+    if (e != OCA_OK) return e;
+    *bytes = (int64_t)tape_layout(scene, model->kind, max_iter).bytes;
+    return OCA_OK;
+}
+
+static oca_status check_admm_args(const oca_ctx *ctx, const oca_scene *scene, const oca_admm_params *params,
+                                  const void *s_ref, const void *s, const void *u, const void *y, const void *zeta,
+                                  const void *xi, const oca_admm_report *report) {
+    if (!ctx || !scene || !params || !s_ref || !s || !u || !y || !zeta || !xi || !report) return OCA_ERR_INVALID_ARGUMENT;
+    if (!report->iters || !report->status || !report->r_pri || !report->r_dual || !report->cost)
+        return OCA_ERR_INVALID_ARGUMENT;
+    if (!(params->sigma > 0.0) || !(params->prox >= 0.0) || !(params->eps_pri >= 0.0) || !(params->eps_dual >= 0.0) ||
+        params->max_iter < 0 || !std::isfinite(params->sigma) || !std::isfinite(params->prox) ||
+        !(params->rho_box >= 0.0) || !(params->damp >= 0.0) || !std::isfinite(params->rho_box) ||
+        !std::isfinite(params->damp))
+        return OCA_ERR_INVALID_ARGUMENT;
+    return OCA_OK;
+}
+
+oca_status oca_admm_solve_taped(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                                const oca_admm_params *params, const void *s_ref, void *s, void *u, void *y,
+                                void *zeta, void *xi, const oca_admm_report *report, void *tape, int64_t tape_bytes,
+                                void *stream) {
+    oca_status e = check_admm_args(ctx, scene, params, s_ref, s, u, y, zeta, xi, report);
+    if (e != OCA_OK) return e;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    if ((e = check_model(sc, model)) != OCA_OK) return e;
+    if (!tape || reinterpret_cast<uintptr_t>(tape) % 256 != 0) return OCA_ERR_INVALID_ARGUMENT;
+    if (tape_bytes < (int64_t)tape_layout(sc, model->kind, params->max_iter).bytes) return OCA_ERR_CAPACITY;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32) return admm_impl<float>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st, tape);
+    return admm_impl<double>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st, tape);
+}
+
+oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                             const oca_admm_params *params, const void *s_ref, void *tape, int64_t tape_bytes,
+                             const int32_t *iters, const void *grad_cost, const void *grad_alpha,
+                             void *grad_obs_offset, void *grad_obs_center, void *grad_state0, void *stream) {
+    if (!ctx || !scene || !params || !s_ref || !tape || !iters || !grad_cost) return OCA_ERR_INVALID_ARGUMENT;
+    if (!grad_obs_offset && !grad_obs_center && !grad_state0) return OCA_ERR_INVALID_ARGUMENT;
+    if (reinterpret_cast<uintptr_t>(tape) % 256 != 0 || params->max_iter < 0) return OCA_ERR_INVALID_ARGUMENT;
+    if (!(params->sigma > 0.0) || !(params->rho_box >= 0.0) || !(params->damp >= 0.0)) return OCA_ERR_INVALID_ARGUMENT;
+    if (!(params->prox > 0.0) || grad_alpha) return OCA_ERR_UNSUPPORTED;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    oca_status e = check_model(sc, model);
+    if (e != OCA_OK) return e;
+    if (tape_bytes < (int64_t)tape_layout(sc, model->kind, params->max_iter).bytes) return OCA_ERR_CAPACITY;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32)
+        return backward_impl<float>(sc, model, params, s_ref, tape, iters, grad_cost, grad_obs_offset, grad_obs_center,
+                                    grad_state0, st);
+    return backward_impl<double>(sc, model, params, s_ref, tape, iters, grad_cost, grad_obs_offset, grad_obs_center,
+                                 grad_state0, st);
 }
 
 }  // extern "C"

@@ -180,4 +180,59 @@ struct RicArgs {
     const long long *scratch0;  // per-scenario offset into scratch (elements)
 };
 
+// ---- adjoint (oca_admm_backward) --------------------------------------------
+// Slots of a taped solve: iterate k of every array lives at base + k * slot.
+template <typename T>
+struct TapeView {
+    const T *y;      // y^k, k = 0..K            [NY][P] per slot
+    const T *zx;     // (zeta^k, xi^k) after the head of iteration k, k = 0..K-1  [1+D][P]
+    const T *stats;  // Gauss-Newton statistics of iteration k  [NSTAT][Qtot]
+    const T *s, *u;  // s^k, u^k, k = 0..K      [n_states][NS], [n_ctrls][NU]
+    const T *box;    // z_s, w_s, z_u, w_u after the box update giving iterate k
+    long long y_slot, zx_slot, stats_slot, s_slot, u_slot, box_slot;
+    long long n_states, n_ctrls;  // row counts (box sub-array offsets)
+};
+
+template <typename T>
+struct AdjTrajArgs {
+    const ScenMeta *meta;
+    Geom<T> g;
+    DevModel<T> model;
+    T sigma, rho_box, damp;
+    const T *s_ref;
+    int Qtot;
+    const int *iters;       // [S] iterations of the taped solve
+    int k;                  // reverse step: iteration k is differentiated
+    TapeView<T> tape;
+    const T *grad_cost;     // [S] (seed only)
+    T *sb, *ub;             // adjoints of s, u (rows as the state arrays)
+    T *zsb, *wsb, *zub, *wub;  // adjoints of the box block
+    T *statsb;              // [NSTAT][Qtot] adjoint of the statistics of iteration k (out)
+    const T *poseb;         // [PK][Qtot] adjoint of the poses of s^{k+1} (in)
+    double *gs0;            // [S][NS] accumulated adjoint of the initial states
+    void *scratch;
+    const long long *scratch0;
+};
+
+template <typename T>
+struct AdjPairArgs {
+    const ScenMeta *meta;
+    const Tile *tiles;
+    Geom<T> g;
+    const T *pose;          // [PK][Qtot] poses of s^k
+    int Qtot;
+    long long P;
+    T prox;
+    const int *iters;
+    int k;
+    const T *y_k, *y_k1;    // y^k (proximal centre, head), y^{k+1} (QP solution)
+    const T *zx_k;          // zeta^k, xi^k
+    const T *ybar_in;       // [NY][P] adjoint of y^{k+1} from iteration k+1
+    T *ybar_out;            // [NY][P] adjoint of y^k (partial: proximal centre and head)
+    T *zb, *xb;             // [P], [D][P] running adjoints of zeta and xi
+    const T *statsb;        // [NSTAT][Qtot]
+    T *poseb;               // [PK][Qtot] adjoint of the poses of s^k (out)
+    double *gd;             // [M_tot][FO] accumulated adjoint of the obstacle offsets
+};
+
 }  // namespace oca

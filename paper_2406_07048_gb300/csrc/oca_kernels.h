@@ -19,4 +19,15 @@ cudaError_t launch_riccati(const RicArgs<T> &a, bool f32, cudaStream_t st);
 
 long long riccati_scratch_elems(int kind, int N);
 
+// adjoint of a taped ADMM solve (oca_adjoint.cu)
+template <typename T>
+cudaError_t launch_adj_seed(const AdjTrajArgs<T> &a, int n_scen, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_traj(const AdjTrajArgs<T> &a, int n_scen, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_pair(const AdjPairArgs<T> &a, int dim, int n_tiles, int W, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adj_finish(const double *gd, const T *obs_C, const int *obs_nf, int M_tot, int FO, int dim,
+                              T *grad_d, T *grad_ctr, cudaStream_t st);
+
 }  // namespace oca

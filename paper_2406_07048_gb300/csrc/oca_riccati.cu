@@ -18,22 +18,9 @@
 //      the forward sweep, writing s^{j+1}, u^{j+1} and the new poses.
 #include "oca_common.cuh"
 #include "oca_kernels.h"
-#include "oca_models.cuh"
+#include "oca_ric.cuh"
 
 namespace oca {
-
-template <int NS, int NU>
-struct RicLayout {
-    // offsets (elements) inside a scenario's scratch block for horizon N
-    __host__ __device__ static long long A(int N, int t) { return (long long)t * NS * NS; }
-    __host__ __device__ static long long B(int N, int t) { return (long long)N * NS * NS + (long long)t * NS * NU; }
-    __host__ __device__ static long long c(int N, int t) { return (long long)N * (NS * NS + NS * NU) + (long long)t * NS; }
-    __host__ __device__ static long long Q(int N, int t) { return (long long)N * (NS * NS + NS * NU + NS) + (long long)t * NS * NS; }
-    __host__ __device__ static long long q(int N, int t) { return Q(N, 0) + (long long)(N + 1) * NS * NS + (long long)t * NS; }
-    __host__ __device__ static long long K(int N, int t) { return q(N, 0) + (long long)(N + 1) * NS + (long long)t * NU * NS; }
-    __host__ __device__ static long long k(int N, int t) { return K(N, 0) + (long long)N * NU * NS + (long long)t * NU; }
-    __host__ __device__ static long long size(int N) { return k(N, 0) + (long long)N * NU; }
-};
 
 long long riccati_scratch_elems(int kind, int N) {
     switch (kind) {
@@ -41,15 +28,6 @@ long long riccati_scratch_elems(int kind, int N) {
         case 1: return RicLayout<5, 2>::size(N);
         default: return RicLayout<12, 4>::size(N);
     }
-}
-
-template <typename T>
-__device__ __forceinline__ bool bounded(T lo, T hi) { return lo > T(-1e29) || hi < T(1e29); }
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 template <typename T, int KIND>
@@ -82,9 +60,7 @@ __device__ void finish_scenario(const RicArgs<T> &a, const ScenMeta &sm, int s, 
 
 template <typename T, typename F, int KIND>
 __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
-    constexpr int NS = MDims<KIND>::NS, NU = MDims<KIND>::NU, D = MDims<KIND>::D, NROT = MDims<KIND>::NROT;
-    constexpr int NW = StatDims<D>::NW;
-    using LY = RicLayout<NS, NU>;
+    constexpr int NS = MDims<KIND>::NS, NU = MDims<KIND>::NU, D = MDims<KIND>::D;
     const int s = blockIdx.x;
     const int lane = threadIdx.x;
     if (a.scen_status[s] != kActive) return;
@@ -114,316 +90,46 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
         return;
     }
 
-    DevModel<F> mdl;
-    mdl.kind = a.model.kind;
-    mdl.dt = F(a.model.dt);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) mdl.p[i] = F(a.model.p[i]);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) mdl.Qs[i] = F(a.model.Qs[i]);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) mdl.Qu[i] = F(a.model.Qu[i]);
-    const F rho_b = F(a.rho_box), damp = F(a.damp);
     F *scr = reinterpret_cast<F *>(a.scratch) + a.scratch0[s];
 
-    // ---- 2. stage assembly, lanes over t
-    // (in the array precision T: only the factorisation below runs in F)
-    const DevModel<T> &mdt = a.model;
-    for (int t = lane; t <= N; t += 32) {
-        T st[NS];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) st[i] = a.s[(long long)(sm.state0 + t) * NS + i];
-        if (t < N) {
-            T ut[NU], f[NS], fs[NS * NS], fu[NS * NU];
-#pragma unroll
-            for (int i = 0; i < NU; ++i) ut[i] = a.u[(long long)(sm.ctrl0 + t) * NU + i];
-            dynamics<T, KIND>(mdt, st, ut, f, fs, fu);
-            F *At = scr + LY::A(N, t), *Bt = scr + LY::B(N, t), *ct = scr + LY::c(N, t);
-            for (int i = 0; i < NS; ++i) {
-                T acc = st[i] + mdt.dt * f[i];
-                for (int k = 0; k < NS; ++k) {
-                    const T v = (i == k ? T(1) : T(0)) + mdt.dt * fs[i * NS + k];
-                    At[i * NS + k] = F(v);
-                    acc -= v * st[k];
-                }
-                for (int k = 0; k < NU; ++k) {
-                    const T v = mdt.dt * fu[i * NU + k];
-                    Bt[i * NU + k] = F(v);
-                    acc -= v * ut[k];
-                }
-                ct[i] = F(acc);
-            }
-        }
-        // stage cost accumulated in registers (T), stored once in F
-        T Qr[NS * NS], qr[NS];
-        for (int i = 0; i < NS * NS; ++i) Qr[i] = T(0);
-        for (int i = 0; i < NS; ++i) {
-            Qr[i * NS + i] = T(2) * mdt.Qs[i];
-            qr[i] = -T(2) * mdt.Qs[i] * a.s_ref[(long long)(sm.state0 + t) * NS + i];
-            if (t >= 1) {
-                // proximal damping 0.5 damp |s - s^j|^2 and the box block's
-                // augmented term 0.5 rho_b |s - z + w|^2 on bounded components
-                Qr[i * NS + i] += a.damp;
-                qr[i] -= a.damp * st[i];
-                if (bounded(a.model.s_lo[i], a.model.s_hi[i])) {
-                    const long long k2 = (long long)(sm.state0 + t) * NS + i;
-                    Qr[i * NS + i] += a.rho_box;
-                    qr[i] -= a.rho_box * (a.box_zs[k2] - a.box_ws[k2]);
-                }
-            }
-        }
-        if (t >= 1) {
-            for (int part = 0; part < sm.NP; ++part) {
-                const int gp = sm.part0 + part;
-                T off[D], rho[D], R[D * D], drho[D * NS], dR[NROT][D * D];
-                int ridx[NROT];
-#pragma unroll
-                for (int i = 0; i < D; ++i) off[i] = a.g.part_off[gp * D + i];
-                part_pose<T, KIND>(mdt, a.g.part_link[gp], off, st, rho, R, drho, dR, ridx);
-                const long long col = sm.qbeg + part * N + (t - 1);
-                T W[D][D], Wc[D], E[D][D];
-                int k = 0;
-#pragma unroll
-                for (int i = 0; i < D; ++i)
-#pragma unroll
-                    for (int jj = 0; jj <= i; ++jj) {
-                        W[i][jj] = W[jj][i] = a.stats[(long long)k * a.Qtot + col];
-                        ++k;
-                    }
-#pragma unroll
-                for (int i = 0; i < D; ++i) Wc[i] = a.stats[(long long)(NW + i) * a.Qtot + col];
-#pragma unroll
-                for (int i = 0; i < D; ++i)
-#pragma unroll
-                    for (int jj = 0; jj < D; ++jj) E[i][jj] = a.stats[(long long)(NW + D + i * D + jj) * a.Qtot + col];
-                // translation block: drho^T W drho, gradient -drho^T (Wc - W rho)
-                T WD[D][NS], gvec[D];
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    T acc = Wc[i];
-#pragma unroll
-                    for (int jj = 0; jj < D; ++jj) acc -= W[i][jj] * rho[jj];
-                    gvec[i] = acc;
-                    for (int b2 = 0; b2 < NS; ++b2) {
-                        T v = T(0);
-#pragma unroll
-                        for (int jj = 0; jj < D; ++jj) v += W[i][jj] * drho[jj * NS + b2];
-                        WD[i][b2] = v;
-                    }
-                }
-                T Hs[NS];
-                for (int a2 = 0; a2 < NS; ++a2) {
-                    for (int b2 = 0; b2 < NS; ++b2) {
-                        T v = T(0);
-#pragma unroll
-                        for (int i = 0; i < D; ++i) v += drho[i * NS + a2] * WD[i][b2];
-                        Hs[b2] = v;
-                    }
-                    // rotation block: tr(R_a R_b^T W), gradient tr(R_a E^T) + tr(R_a R^T W)
-#pragma unroll
-                    for (int ra = 0; ra < NROT; ++ra) {
-                        if (ridx[ra] != a2) continue;
-#pragma unroll
-                        for (int rb = 0; rb < NROT; ++rb) {
-                            T v = T(0);
-#pragma unroll
-                            for (int i = 0; i < D; ++i)
-#pragma unroll
-                                for (int jj = 0; jj < D; ++jj) {
-                                    T m = T(0);
-#pragma unroll
-                                    for (int l = 0; l < D; ++l) m += dR[ra][i * D + l] * dR[rb][jj * D + l];
-                                    v += m * W[i][jj];
-                                }
-                            Hs[ridx[rb]] += v;
-                        }
-                    }
-                    T g = T(0);
-#pragma unroll
-                    for (int i = 0; i < D; ++i) g -= drho[i * NS + a2] * gvec[i];
-#pragma unroll
-                    for (int ra = 0; ra < NROT; ++ra) {
-                        if (ridx[ra] != a2) continue;
-                        T v = T(0);
-#pragma unroll
-                        for (int i = 0; i < D; ++i)
-#pragma unroll
-                            for (int jj = 0; jj < D; ++jj) {
-                                T m = T(0);
-#pragma unroll
-                                for (int l = 0; l < D; ++l) m += dR[ra][i * D + l] * R[jj * D + l];
-                                v += dR[ra][i * D + jj] * E[i][jj] + m * W[i][jj];
-                            }
-                        g += v;
-                    }
-                    T hsx = T(0);
-                    for (int b2 = 0; b2 < NS; ++b2) {
-                        Qr[a2 * NS + b2] += a.sigma * Hs[b2];
-                        hsx += Hs[b2] * st[b2];
-                    }
-                    qr[a2] += a.sigma * (g - hsx);
-                }
-            }
-        }
-        F *Qt = scr + LY::Q(N, t), *qt = scr + LY::q(N, t);
-        for (int i = 0; i < NS * NS; ++i) Qt[i] = F(Qr[i]);
-        for (int i = 0; i < NS; ++i) qt[i] = F(qr[i]);
-    }
+    // ---- 2. stage assembly, lanes over t (in the array precision T; only
+    // the factorisation below runs in F)
+    StageParams<T> sp;
+    sp.model = a.model;
+    sp.g = a.g;
+    sp.sigma = a.sigma;
+    sp.rho_box = a.rho_box;
+    sp.damp = a.damp;
+    sp.s_ref = a.s_ref;
+    sp.Qtot = a.Qtot;
+    StageSrc<T> src;
+    src.s = a.s;
+    src.u = a.u;
+    src.zs = a.box_zs;
+    src.ws = a.box_ws;
+    src.zu = a.box_zu;
+    src.wu = a.box_wu;
+    src.stats = a.stats;
+    for (int t = lane; t <= N; t += 32) assemble_stage<T, F, KIND>(sp, src, sm, t, scr);
     __syncwarp();
 
-    // ---- 3. backward Riccati recursion
-    __shared__ F P[NS * NS], pv[NS], PA[NS * NS], PB[NS * NU], wv[NS];
-    __shared__ F Quu[NU * NU], Qus[NU * NS], qu[NU], Qss[NS * NS], qs[NS], Kt[NU * NS], kt[NU];
-    __shared__ int bad;
-    if (lane == 0) bad = 0;
-    for (int e = lane; e < NS * NS; e += 32) P[e] = scr[LY::Q(N, N) + e];
-    for (int e = lane; e < NS; e += 32) pv[e] = scr[LY::q(N, N) + e];
-    __syncwarp();
-    for (int t = N - 1; t >= 0; --t) {
-        const F *At = scr + LY::A(N, t), *Bt = scr + LY::B(N, t), *ct = scr + LY::c(N, t);
-        for (int e = lane; e < NS * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F acc = F(0);
-            for (int k = 0; k < NS; ++k) acc += P[i * NS + k] * At[k * NS + jj];
-            PA[e] = acc;
-        }
-        for (int e = lane; e < NS * NU; e += 32) {
-            const int i = e / NU, jj = e % NU;
-            F acc = F(0);
-            for (int k = 0; k < NS; ++k) acc += P[i * NS + k] * Bt[k * NU + jj];
-            PB[e] = acc;
-        }
-        for (int i = lane; i < NS; i += 32) {
-            F acc = pv[i];
-            for (int k = 0; k < NS; ++k) acc += P[i * NS + k] * ct[k];
-            wv[i] = acc;
-        }
-        __syncwarp();
-        const F *Qt = scr + LY::Q(N, t), *qt = scr + LY::q(N, t);
-        for (int e = lane; e < NS * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F acc = Qt[e];
-            for (int k = 0; k < NS; ++k) acc += At[k * NS + i] * PA[k * NS + jj];
-            Qss[e] = acc;
-        }
-        for (int e = lane; e < NU * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F acc = F(0);
-            for (int k = 0; k < NS; ++k) acc += Bt[k * NU + i] * PA[k * NS + jj];
-            Qus[e] = acc;
-        }
-        for (int e = lane; e < NU * NU; e += 32) {
-            const int i = e / NU, jj = e % NU;
-            F acc = (i == jj) ? F(2) * mdl.Qu[i] + damp + (bounded(a.model.u_lo[i], a.model.u_hi[i]) ? rho_b : F(0)) : F(0);
-            for (int k = 0; k < NS; ++k) acc += Bt[k * NU + i] * PB[k * NU + jj];
-            Quu[e] = acc;
-        }
-        for (int i = lane; i < NS + NU; i += 32) {
-            if (i < NS) {
-                F acc = qt[i];
-                for (int k = 0; k < NS; ++k) acc += At[k * NS + i] * wv[k];
-                qs[i] = acc;
-            } else {
-                const int ii = i - NS;
-                const long long k2 = (long long)(sm.ctrl0 + t) * NU + ii;
-                F acc = -damp * F(a.u[k2]);
-                if (bounded(a.model.u_lo[ii], a.model.u_hi[ii])) acc -= rho_b * (F(a.box_zu[k2]) - F(a.box_wu[k2]));
-                for (int k = 0; k < NS; ++k) acc += Bt[k * NU + ii] * wv[k];
-                qu[ii] = acc;
-            }
-        }
-        __syncwarp();
-        // Cholesky of Quu (NU <= 4) by lane 0
-        if (lane == 0) {
-            for (int c = 0; c < NU; ++c) {
-                F dg = Quu[c * NU + c];
-                for (int k = 0; k < c; ++k) dg -= Quu[c * NU + k] * Quu[c * NU + k];
-                if (!(dg > F(0))) {
-                    bad = 1;
-                    dg = F(1);
-                }
-                dg = m_sqrt(dg);
-                Quu[c * NU + c] = dg;
-                for (int r = c + 1; r < NU; ++r) {
-                    F acc = Quu[r * NU + c];
-                    for (int k = 0; k < c; ++k) acc -= Quu[r * NU + k] * Quu[c * NU + k];
-                    Quu[r * NU + c] = acc / dg;
-                }
-            }
-        }
-        __syncwarp();
-        // K = -Quu^-1 Qus (columns over lanes), k = -Quu^-1 qu (lane NS)
-        for (int col = lane; col <= NS; col += 32) {
-            F x[NU];
-            for (int i = 0; i < NU; ++i) x[i] = -(col < NS ? Qus[i * NS + col] : qu[i]);
-            for (int i = 0; i < NU; ++i) {
-                F acc = x[i];
-                for (int k = 0; k < i; ++k) acc -= Quu[i * NU + k] * x[k];
-                x[i] = acc / Quu[i * NU + i];
-            }
-            for (int i = NU - 1; i >= 0; --i) {
-                F acc = x[i];
-                for (int k = i + 1; k < NU; ++k) acc -= Quu[k * NU + i] * x[k];
-                x[i] = acc / Quu[i * NU + i];
-            }
-            for (int i = 0; i < NU; ++i) {
-                if (col < NS) {
-                    Kt[i * NS + col] = x[i];
-                    scr[LY::K(N, t) + i * NS + col] = x[i];
-                } else {
-                    kt[i] = x[i];
-                    scr[LY::k(N, t) + i] = x[i];
-                }
-            }
-        }
-        __syncwarp();
-        // P = Qss + Qus^T K (symmetrised), p = qs + Qus^T k
-        for (int e = lane; e < NS * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F a1 = Qss[i * NS + jj], a2 = Qss[jj * NS + i];
-            for (int k = 0; k < NU; ++k) {
-                a1 += Qus[k * NS + i] * Kt[k * NS + jj];
-                a2 += Qus[k * NS + jj] * Kt[k * NS + i];
-            }
-            P[e] = F(0.5) * (a1 + a2);
-        }
-        for (int i = lane; i < NS; i += 32) {
-            F acc = qs[i];
-            for (int k = 0; k < NU; ++k) acc += Qus[k * NS + i] * kt[k];
-            pv[i] = acc;
-        }
-        __syncwarp();
-    }
-
-    // ---- 4. forward sweep: u_t = K_t s_t + k_t, s_{t+1} = A_t s_t + B_t u_t + c_t
-    __shared__ F sc[NS], uc[NU];
+    // ---- 3. backward Riccati recursion, 4. forward sweep
+    F ru_diag[NU];
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+        ru_diag[i] = F(2) * F(a.model.Qu[i]) + F(a.damp) +
+                     (bounded(a.model.u_lo[i], a.model.u_hi[i]) ? F(a.rho_box) : F(0));
+    bool ok = ric_factor<F, NS, NU>(scr, N, ru_diag);
+    __shared__ F sc[NS];
     for (int i = lane; i < NS; i += 32) sc[i] = F(a.s[(long long)sm.state0 * NS + i]);
     __syncwarp();
-    bool finite = true;
-    for (int t = 0; t < N; ++t) {
-        if (lane < NU) {
-            F acc = scr[LY::k(N, t) + lane];
-            for (int k = 0; k < NS; ++k) acc += scr[LY::K(N, t) + lane * NS + k] * sc[k];
-            uc[lane] = acc;
-            a.u[(long long)(sm.ctrl0 + t) * NU + lane] = T(acc);
-            finite &= m_finite(acc);
-        }
-        __syncwarp();
-        F nx = F(0);
-        if (lane < NS) {
-            nx = scr[LY::c(N, t) + lane];
-            for (int k = 0; k < NS; ++k) nx += scr[LY::A(N, t) + lane * NS + k] * sc[k];
-            for (int k = 0; k < NU; ++k) nx += scr[LY::B(N, t) + lane * NU + k] * uc[k];
-        }
-        __syncwarp();
-        if (lane < NS) {
-            sc[lane] = nx;
-            a.s[(long long)(sm.state0 + t + 1) * NS + lane] = T(nx);
-            finite &= m_finite(nx);
-        }
-        __syncwarp();
-    }
-    const bool ok = __all_sync(0xffffffffu, finite) && !bad;
+    struct Out {
+        T *s, *u;
+        long long s0, c0;
+        __device__ void put_u(int t, int i, F v) { u[(c0 + t) * NU + i] = T(v); }
+        __device__ void put_s(int t, int i, F v) { s[(s0 + t) * NS + i] = T(v); }
+    } out{a.s, a.u, (long long)sm.state0, (long long)sm.ctrl0};
+    ok = ric_sweep<F, NS, NU>(scr, N, sc, out) && ok;
     if (!ok) {
         finish_scenario<T, KIND>(a, sm, s, OCA_SCEN_FAILED, j, 0.0, 0.0);
         return;
