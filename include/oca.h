@@ -268,21 +268,24 @@ oca_status oca_admm_solve_taped(oca_ctx *ctx, const oca_scene *scene, const oca_
                                 const oca_admm_params *params, const void *s_ref, void *s, void *u, void *y,
                                 void *zeta, void *xi, const oca_admm_report *report, void *tape, int64_t tape_bytes,
                                 void *stream);
-/* Gradient of L = sum_s grad_cost[s] * F_s, F_s the trajectory cost of
- * eqn:navigation_cost returned by the taped solve for scenario s, with
- * respect to the obstacle offsets d, the obstacle translations and the
- * initial states.  Arguments: the scene, model, params and s_ref of the
- * taped solve; tape, tape_bytes as given to it (its work area is
- * overwritten); iters = report.iters of that solve (device, [S]);
- * grad_cost [S] (device, scene dtype).
+/* Gradient of L = sum_s grad_cost[s] * F_s + sum_p grad_alpha[p] * alpha*_p,
+ * F_s the trajectory cost of eqn:navigation_cost returned by the taped
+ * solve for scenario s and alpha*_p the scale of eqn:scale_opt of pair p at
+ * the returned trajectory, with respect to the obstacle offsets d, the
+ * obstacle translations and the initial states.  alpha* enters through the
+ * LP envelope theorem (Sec. III-B): its derivative is -mu_m with respect to
+ * d'_m and mu_m x_i with respect to C'_mi, at the optimal certificate mu and
+ * primal point x; valid where the LP's optimal basis is unique.  Arguments: the scene, model, params and
+ * s_ref of the taped solve; tape, tape_bytes as given to it (its work area
+ * is overwritten); iters = report.iters of that solve (device, [S]);
+ * grad_cost [S] (device, scene dtype); grad_alpha [P] or NULL.
  * Outputs (device, scene dtype, each may be NULL but not all three):
  *   grad_obs_offset [M_tot][fo_max]  dL/dd_m (pad faces 0);
  *   grad_obs_center [M_tot][dim]     dL/ddelta for a translation delta of the
  *                                    obstacle (offsets d_m + c_m . delta);
  *   grad_state0     [S][ns]          dL/ds_0.
- * grad_alpha must be NULL (per-pair alpha* gradients are not part of this
- * build: OCA_ERR_UNSUPPORTED); prox must be > 0 (OCA_ERR_UNSUPPORTED).
- * Scenarios whose solve FAILED get meaningless gradients. */
+ * prox must be > 0 (else OCA_ERR_UNSUPPORTED).  Scenarios whose solve
+ * FAILED, or that ran no iteration, get meaningless gradients. */
 oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
                              const oca_admm_params *params, const void *s_ref, void *tape, int64_t tape_bytes,
                              const int32_t *iters, const void *grad_cost, const void *grad_alpha,

@@ -338,10 +338,11 @@ def new_tape(ds: DeviceScene, max_iter: int) -> torch.Tensor:
     return torch.empty(tape_bytes(ds, max_iter), dtype=torch.uint8, device=ds.device)
 
 
-def admm_backward(ds: DeviceScene, s_ref, tape, iters, grad_cost, sigma=300.0, prox=0.1, max_iter=300,
-                  rho_box=100.0, damp=100.0, eps_pri=1e-4, eps_dual=1e-4, flags=0, stream=None):
-    """oca_admm_backward: gradients of sum_s grad_cost[s] * cost_s of a taped
-    solve w.r.t. obstacle offsets [M_tot, fo_max], obstacle translations
+def admm_backward(ds: DeviceScene, s_ref, tape, iters, grad_cost, grad_alpha=None, sigma=300.0, prox=0.1,
+                  max_iter=300, rho_box=100.0, damp=100.0, eps_pri=1e-4, eps_dual=1e-4, flags=0, stream=None):
+    """oca_admm_backward: gradients of sum_s grad_cost[s] * cost_s (+ sum_p
+    grad_alpha[p] * alpha*_p at the returned trajectory) of a taped solve
+    w.r.t. obstacle offsets [M_tot, fo_max], obstacle translations
     [M_tot, dim] and initial states [S, ns]."""
     sc = ds.scene
     m_tot = int(sc.obs_begin[-1])
@@ -351,8 +352,9 @@ def admm_backward(ds: DeviceScene, s_ref, tape, iters, grad_cost, sigma=300.0, p
     pr = AdmmParams(float(sigma), float(eps_pri), float(eps_dual), float(prox), int(max_iter), int(flags),
                     float(rho_box), float(damp))
     gc = grad_cost.to(ds.dtype).contiguous()
+    ga = None if grad_alpha is None else grad_alpha.to(ds.dtype).contiguous()
     _check(lib().oca_admm_backward(ds.ctx.h, ds.h, C.byref(ds.model), C.byref(pr), _ptr(s_ref), _ptr(tape),
-                                   C.c_int64(tape.numel()), _ptr(iters), _ptr(gc), None, _ptr(g_d), _ptr(g_c),
+                                   C.c_int64(tape.numel()), _ptr(iters), _ptr(gc), _ptr(ga), _ptr(g_d), _ptr(g_c),
                                    _ptr(g_s0), _stream(stream)), "oca_admm_backward")
     return dict(obs_offset=g_d, obs_center=g_c, state0=g_s0)
 

@@ -725,6 +725,118 @@ __global__ void __launch_bounds__(256) k_adj_pair(AdjPairArgs<T> a) {
     }
 }
 
+
+// ============================================================================
+// alpha* of the returned trajectory (Sec. III-A eqn:scale_opt): by the LP
+// envelope theorem, at the optimum (alpha*, x*; lambda*, mu*) of a pair
+//   dalpha/dd_m = -mu_m,  dalpha/drho = C^T mu,  dalpha/dR = (C^T mu) x*^T
+// (C' = C R, d' = d - C rho; the Lagrangian alpha + lambda^T (A x - alpha b)
+// + mu^T (C' x - d') differentiated at fixed multipliers).  Writes the pose
+// adjoints that seed the reverse sweep and adds the offset adjoints.
+// ============================================================================
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_adj_alpha(AdjAlphaArgs<T> a) {
+    constexpr int PK = D + D * D;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *red = reinterpret_cast<T *>(smem_raw);  // [W][PK][32]
+    const Tile tile = a.tiles[blockIdx.x];
+    const ScenMeta sm = a.meta[tile.scen];
+    const int lane = threadIdx.x, warp = threadIdx.y, W = blockDim.y;
+    const int Q = sm.NP * sm.N;
+    const int q = tile.q0 + lane;
+    const bool valid = q < Q;
+    const int qc = valid ? q : Q - 1;
+    const long long P = a.P;
+    const int FR = a.g.FR, FO = a.g.FO;
+    T pb[PK];
+#pragma unroll
+    for (int i = 0; i < PK; ++i) pb[i] = T(0);
+    Lane<T, D> L;
+    const int col = sm.qbeg + qc;
+#pragma unroll
+    for (int i = 0; i < D; ++i) L.rho[i] = a.pose[(long long)i * a.Qtot + col];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) L.R[i] = a.pose[(long long)(D + i) * a.Qtot + col];
+    const int gp = sm.part0 + qc / sm.N;
+    L.A = a.g.part_A + (long long)gp * FR * D;
+    L.b = a.g.part_b + (long long)gp * FR;
+    L.nr = a.g.part_nf[gp];
+    for (int j = warp; j < sm.M; j += W) {
+        const int gm = sm.obs0 + j;
+        L.C = a.g.obs_C + (long long)gm * FO * D;
+        L.d = a.g.obs_d + (long long)gm * FO;
+        L.no = a.g.obs_nf[gm];
+        const long long p = sm.pair0 + (long long)j * Q + qc;
+        int bas[D + 1];
+        T xB[D + 1], alpha, x[D];
+        lp_solve<T, D>(L, bas, xB, alpha);
+        const bool okx = lp_primal<T, D>(L, bas, x);
+        const T ga = valid && okx ? a.grad_alpha[p] : T(0);
+        T w[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) w[i] = T(0);
+        for (int m = 0; m < L.no; ++m) {
+            T mu = T(0);
+#pragma unroll
+            for (int i = 0; i < D + 1; ++i)
+                if (bas[i] == L.nr + m) mu = xB[i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) w[i] += mu * L.C[m * D + i];
+            T gdv = -ga * mu;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) gdv += __shfl_xor_sync(0xffffffffu, gdv, o);
+            if (lane == 0) atomicAdd(a.gd + (long long)gm * FO + m, double(gdv));
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            pb[i] += ga * w[i];
+#pragma unroll
+            for (int l = 0; l < D; ++l) pb[D + i * D + l] += ga * w[i] * x[l];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PK; ++i) red[(warp * PK + i) * 32 + lane] = pb[i];
+    __syncthreads();
+    if (valid) {
+        for (int i = warp; i < PK; i += W) {
+            T acc = T(0);
+            for (int w2 = 0; w2 < W; ++w2) acc += red[(w2 * PK + i) * 32 + lane];
+            a.poseb[(long long)i * a.Qtot + sm.qbeg + q] = acc;
+        }
+    }
+}
+
+// returned states of every scenario (iterate iters[s] of the tape) into one array
+template <typename T>
+__global__ void k_adj_final_states(const ScenMeta *meta, const int *iters, const T *tape_s, long long s_slot, int NS,
+                                   T *out) {
+    const int s = blockIdx.y;
+    const ScenMeta sm = meta[s];
+    const T *src = tape_s + (long long)iters[s] * s_slot;
+    const int n = (sm.N + 1) * NS;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long k2 = (long long)sm.state0 * NS + e;
+        out[k2] = src[k2];
+    }
+}
+
+template <typename T>
+cudaError_t launch_adj_alpha(const AdjAlphaArgs<T> &a, int dim, int n_tiles, int W, const int *iters,
+                             const T *tape_s, long long s_slot, int NS, int n_scen, T *states_out,
+                             const PoseArgs<T> &pa, int maxQ, cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    k_adj_final_states<T><<<dim3(4, n_scen), 128, 0, st>>>(a.meta, iters, tape_s, s_slot, NS, states_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    PoseArgs<T> p2 = pa;
+    p2.states = states_out;
+    if ((e = launch_pose<T>(p2, maxQ, st)) != cudaSuccess) return e;
+    const size_t sm = (size_t)W * (dim + dim * dim) * 32 * sizeof(T);
+    if (dim == 2) k_adj_alpha<T, 2><<<n_tiles, dim3(32, W), sm, st>>>(a);
+    else k_adj_alpha<T, 3><<<n_tiles, dim3(32, W), sm, st>>>(a);
+    return cudaGetLastError();
+}
+
 // ============================================================================
 // launchers
 // ============================================================================
@@ -801,6 +913,11 @@ template cudaError_t launch_adj_traj<float>(const AdjTrajArgs<float> &, int, cud
 template cudaError_t launch_adj_traj<double>(const AdjTrajArgs<double> &, int, cudaStream_t);
 template cudaError_t launch_adj_pair<float>(const AdjPairArgs<float> &, int, int, int, cudaStream_t);
 template cudaError_t launch_adj_pair<double>(const AdjPairArgs<double> &, int, int, int, cudaStream_t);
+template cudaError_t launch_adj_alpha<float>(const AdjAlphaArgs<float> &, int, int, int, const int *, const float *,
+                                             long long, int, int, float *, const PoseArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_adj_alpha<double>(const AdjAlphaArgs<double> &, int, int, int, const int *, const double *,
+                                              long long, int, int, double *, const PoseArgs<double> &, int,
+                                              cudaStream_t);
 template cudaError_t launch_adj_finish<float>(const double *, const float *, const int *, int, int, int, float *, float *,
                                               cudaStream_t);
 template cudaError_t launch_adj_finish<double>(const double *, const double *, const int *, int, int, int, double *,

@@ -300,7 +300,7 @@ oca_status pairqp_impl(oca_scene *sc, const oca_model *m, const void *states, co
 struct TapeLayout {
     long long y, zx, st, s, u, box;                   // iterate regions
     long long y_slot, zx_slot, st_slot, s_slot, u_slot, box_slot;
-    long long yb, zb, sb, ub, bb, stb, pb;            // adjoint work area
+    long long yb, zb, sb, ub, bb, stb, pb, sf;        // adjoint work area
     long long work_end;                               // end of the T regions
     size_t gd_byte, gs0_byte, bytes;
 };
@@ -332,6 +332,7 @@ TapeLayout tape_layout(const oca_scene *sc, int kind, int K) {
     L.bb = o;  o += L.box_slot;
     L.stb = o; o += L.st_slot;
     L.pb = o;  o += up((long long)PK * sc->Qtot);
+    L.sf = o;  o += L.s_slot;
     L.work_end = o;
     size_t b = (size_t)o * (size_t)es;
     b = (b + 255) / 256 * 256;
@@ -560,8 +561,8 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
 
 template <typename T>
 oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *tape,
-                         const int32_t *iters, const void *grad_cost, void *grad_d, void *grad_ctr, void *grad_s0,
-                         cudaStream_t st) {
+                         const int32_t *iters, const void *grad_cost, const void *grad_alpha, void *grad_d,
+                         void *grad_ctr, void *grad_s0, cudaStream_t st) {
     const int K = pr->max_iter;
     const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
     const TapeLayout TL = tape_layout(sc, m->kind, K);
@@ -624,6 +625,22 @@ oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_param
     pa.pose = static_cast<T *>(sc->d_pose);
     pa.Qtot = sc->Qtot;
     pa.scen_status = nullptr;
+    const int W = std::min(sc->W, 8);
+    if (grad_alpha) {
+        // alpha* at the returned states seeds the pose adjoints and the offsets
+        AdjAlphaArgs<T> aa;
+        aa.meta = sc->d_meta;
+        aa.tiles = sc->d_tiles;
+        aa.g = make_geom<T>(sc);
+        aa.pose = static_cast<const T *>(sc->d_pose);
+        aa.Qtot = sc->Qtot;
+        aa.P = sc->P;
+        aa.grad_alpha = static_cast<const T *>(grad_alpha);
+        aa.poseb = tp + TL.pb;
+        aa.gd = gd;
+        OCA_CK(launch_adj_alpha<T>(aa, sc->dim, sc->n_tiles, W, iters, tp + TL.s, TL.s_slot, NS, sc->S, tp + TL.sf, pa,
+                                   sc->maxQ, st));
+    }
 
     AdjPairArgs<T> ap;
     std::memset(&ap, 0, sizeof(ap));
@@ -640,7 +657,6 @@ oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_param
     ap.statsb = tp + TL.stb;
     ap.poseb = tp + TL.pb;
     ap.gd = gd;
-    const int W = std::min(sc->W, 8);
     for (int k = K - 1; k >= 0; --k) {
         ta.k = k;
         OCA_CK(launch_adj_traj<T>(ta, sc->S, st));
@@ -1048,17 +1064,17 @@ oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_mod
     if (!grad_obs_offset && !grad_obs_center && !grad_state0) return OCA_ERR_INVALID_ARGUMENT;
     if (reinterpret_cast<uintptr_t>(tape) % 256 != 0 || params->max_iter < 0) return OCA_ERR_INVALID_ARGUMENT;
     if (!(params->sigma > 0.0) || !(params->rho_box >= 0.0) || !(params->damp >= 0.0)) return OCA_ERR_INVALID_ARGUMENT;
-    if (!(params->prox > 0.0) || grad_alpha) return OCA_ERR_UNSUPPORTED;
+    if (!(params->prox > 0.0)) return OCA_ERR_UNSUPPORTED;
     oca_scene *sc = const_cast<oca_scene *>(scene);
     oca_status e = check_model(sc, model);
     if (e != OCA_OK) return e;
     if (tape_bytes < (int64_t)tape_layout(sc, model->kind, params->max_iter).bytes) return OCA_ERR_CAPACITY;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (sc->dtype == OCA_F32)
-        return backward_impl<float>(sc, model, params, s_ref, tape, iters, grad_cost, grad_obs_offset, grad_obs_center,
-                                    grad_state0, st);
-    return backward_impl<double>(sc, model, params, s_ref, tape, iters, grad_cost, grad_obs_offset, grad_obs_center,
-                                 grad_state0, st);
+        return backward_impl<float>(sc, model, params, s_ref, tape, iters, grad_cost, grad_alpha, grad_obs_offset,
+                                    grad_obs_center, grad_state0, st);
+    return backward_impl<double>(sc, model, params, s_ref, tape, iters, grad_cost, grad_alpha, grad_obs_offset,
+                                 grad_obs_center, grad_state0, st);
 }
 
 }  // extern "C"

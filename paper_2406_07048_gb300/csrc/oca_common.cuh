@@ -235,4 +235,17 @@ struct AdjPairArgs {
     double *gd;             // [M_tot][FO] accumulated adjoint of the obstacle offsets
 };
 
+template <typename T>
+struct AdjAlphaArgs {
+    const ScenMeta *meta;
+    const Tile *tiles;
+    Geom<T> g;
+    const T *pose;          // [PK][Qtot] poses of the returned states
+    int Qtot;
+    long long P;
+    const T *grad_alpha;    // [P]
+    T *poseb;               // [PK][Qtot] out: adjoint of those poses
+    double *gd;             // [M_tot][FO] accumulated adjoint of the obstacle offsets
+};
+
 }  // namespace oca

@@ -1378,4 +1378,68 @@ OCA_HD int lp_solve(const Lane<T, D> &L, int bas[D + 1], T xB[D + 1], T &alpha) 
 }
 
 
+// Primal point x* of eqn:scale_opt (body frame) from the final basis of
+// lp_solve: the simplex multipliers pi of the dual LP solve B^T pi = c_B
+// (B the basic columns, c_B their costs) and equal (-alpha*, x*).  Returns
+// false if the basis matrix is singular.
+template <typename T, int D>
+OCA_HD inline bool lp_primal(const Lane<T, D> &L, const int bas[D + 1], T x[D]) {
+    constexpr int V = D + 1;
+    const int ART = L.nr + L.no;
+    T M[V][V], r[V];  // M = B^T
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        T col[V], c;
+        lp_col<T, D>(L, bas[j], ART, col, c);
+#pragma unroll
+        for (int i = 0; i < V; ++i) M[j][i] = col[i];
+        r[j] = bas[j] >= ART ? T(0) : c;
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        int pv = k;
+        T pmax = m_abs(M[k][k]);
+#pragma unroll
+        for (int i = k + 1; i < V; ++i)
+            if (m_abs(M[i][k]) > pmax) {
+                pmax = m_abs(M[i][k]);
+                pv = i;
+            }
+        if (!(pmax > T(0))) return false;
+#pragma unroll
+        for (int i = k + 1; i < V; ++i) {
+            if (i == pv) {
+#pragma unroll
+                for (int jj = 0; jj < V; ++jj) {
+                    const T t = M[k][jj];
+                    M[k][jj] = M[i][jj];
+                    M[i][jj] = t;
+                }
+                const T t = r[k];
+                r[k] = r[i];
+                r[i] = t;
+            }
+        }
+#pragma unroll
+        for (int i = k + 1; i < V; ++i) {
+            const T f = M[i][k] / M[k][k];
+#pragma unroll
+            for (int jj = k; jj < V; ++jj) M[i][jj] -= f * M[k][jj];
+            r[i] -= f * r[k];
+        }
+    }
+#pragma unroll
+    for (int i = V - 1; i >= 0; --i) {
+        T acc = r[i];
+#pragma unroll
+        for (int jj = i + 1; jj < V; ++jj) acc -= M[i][jj] * r[jj];
+        r[i] = acc / M[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i] = r[1 + i];
+    return true;
+}
+
+
+
 }  // namespace oca

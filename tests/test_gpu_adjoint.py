@@ -183,3 +183,34 @@ def test_backward_argument_errors(B, ctx):
     with pytest.raises(B.OcaError) as e:
         B.admm_solve(ds, pb.s_ref, pb.s, pb.u, pb.y, pb.zeta, pb.xi, tape=small, max_iter=4)
     assert e.value.code == 5
+
+
+def test_alpha_gradient_matches_oracle_fd(B, ctx, ora):
+    """L = sum_p g_p alpha*_p at the returned trajectory (plus the cost):
+    oca_admm_backward against central differences of the oracle's ADMM
+    followed by its scale LP at the returned states."""
+    sc = synth.config1()
+    K = 10
+    rng = np.random.default_rng(7)
+    ga = rng.uniform(-1.0, 1.0, sc.n_pairs)
+    ds = B.DeviceScene(ctx, sc, torch.float64)
+    pb = B.Problem(ds)
+    tape = B.new_tape(ds, K)
+    rep = B.admm_solve(ds, pb.s_ref, pb.s, pb.u, pb.y, pb.zeta, pb.xi, tape=tape, max_iter=K, **KW)
+    gc = torch.full((1,), 0.5, dtype=torch.float64, device=ds.device)
+    g = B.admm_backward(ds, pb.s_ref, tape, rep["iters"], gc, grad_alpha=torch.as_tensor(ga, device=ds.device),
+                        max_iter=K, **{k: KW[k] for k in ("sigma", "prox", "rho_box", "damp")})
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+
+    def fd(perturb):
+        def L(eps):
+            s2 = perturb(sc, eps)
+            r = ora.admm_batch(s2, max_iter=K, **KW)
+            return 0.5 * r["cost"].sum() + ga @ ora.scale_batch(s2, r["s"])["alpha"]
+        return (L(H) - L(-H)) / (2 * H)
+
+    offs = [(j, m) for j in range(sc.obs_d.shape[0]) for m in range(int(sc.obs_nf[j]))]
+    _check([(fd(_offset(j, m)), g["obs_offset"][j, m]) for j, m in offs], 1e-4)
+    _check([(fd(_centre(j, i)), g["obs_center"][j, i]) for j in range(sc.obs_d.shape[0]) for i in range(sc.dim)],
+           1e-4)
+    _check([(fd(_state0(0, i)), g["state0"][0, i]) for i in range(sc.model.ns)], 1e-5)

@@ -118,3 +118,39 @@ def test_batch_matches_single_on_config_poses(ora):
         al = ora.scale_lp(sc.part_A[pt], sc.part_b[pt], C @ R, d - C @ rho)[0]
         assert r["alpha"][l] == pytest.approx(al, rel=1e-12, abs=1e-12)
         assert r["margin"][l] == pytest.approx(al, rel=1e-8, abs=1e-8)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_envelope_derivatives_match_central_differences(ora, dim):
+    """Sensitivity of alpha* (Sec. III-B, the dual Lagrangian at fixed
+    multipliers): dalpha/dd'_m = -mu_m and dalpha/dC'_mi = mu_m x_i, with
+    (mu, x) the oracle's certificate and primal point, against central
+    differences of the oracle's own alpha*.  Random pairs have a unique
+    optimal basis with probability one; the few whose basis changes within
+    the step are recognised by a one-sided disagreement and skipped."""
+    rng = np.random.default_rng(40 + dim)
+    h = 1e-7
+    checked = 0
+    for _ in range(60):
+        A, b, C, d = _pins.random_pair(rng, dim)
+        al, lam, mu, x, st = ora.scale_lp(A, b, C, d)
+        assert st == 0
+        f = lambda C2, d2: ora.scale_lp(A, b, C2, d2)[0]
+        gd_fd, gc_fd = np.zeros(len(d)), np.zeros(C.shape)
+        smooth = True
+        for m in range(len(d)):
+            e = np.zeros(len(d))
+            e[m] = h
+            fp, fm = f(C, d + e), f(C, d - e)
+            smooth &= abs((fp - al) - (al - fm)) < 1e-6 * h * (1 + abs(al))
+            gd_fd[m] = (fp - fm) / (2 * h)
+            for i in range(dim):
+                E = np.zeros(C.shape)
+                E[m, i] = h
+                gc_fd[m, i] = (f(C + E, d) - f(C - E, d)) / (2 * h)
+        if not smooth:
+            continue
+        checked += 1
+        assert np.allclose(gd_fd, -mu, atol=1e-6 * (1 + np.abs(mu).max()))
+        assert np.allclose(gc_fd, np.outer(mu, x), atol=1e-6 * (1 + np.abs(np.outer(mu, x)).max()))
+    assert checked >= 40
