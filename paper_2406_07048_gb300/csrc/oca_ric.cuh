@@ -243,140 +243,212 @@ __device__ void assemble_stage(const StageParams<T> &a, const StageSrc<T> &src, 
 
 // ----------------------------------------------------------------------------
 // Backward Riccati recursion over the scratch (one warp; every lane calls):
-// P_N = Q_N, p_N = q_N; for t = N-1..0 with P+ = P_{t+1}, w = p_{t+1} + P+ c_t:
-//   Quu = Ru + B^T P+ B, Qus = B^T P+ A, Qss = Q_t + A^T P+ A,
-//   qu = r_t + B^T w, qs = q_t + A^T w,
-//   K_t = -Quu^-1 Qus, k_t = -Quu^-1 qu  (Cholesky of Quu),
-//   P_t = Qss + Qus^T K_t (symmetrised), p_t = qs + Qus^T k_t.
+// P_N = Q_N, p_N = q_N; for t = N-1..0, with G = [A_t | B_t | c_t] and
+// Y = P_{t+1} G + [0 | 0 | p_{t+1}], the stage matrix
+//   M = [Q_t 0 q_t; 0 Ru r_t] + G^T Y  (rows (s, u), columns (s, u, 1))
+// holds Qss, Qus, Quu and qs, qu; then
+//   K_t = -Quu^-1 Qus, k_t = -Quu^-1 qu,
+//   P_t = Qss + Qus^T K_t, p_t = qs + Qus^T k_t.
+// Only the symmetric half of M and of P is formed.  Every lane inverts the
+// (small, SPD) Quu itself.  The step's data are staged in shared memory and
+// the next step's are loaded while this one computes.
 // ru_diag = diagonal of Ru.  Returns false if a Quu was not positive definite.
 // ----------------------------------------------------------------------------
 template <typename F, int NS, int NU>
+__device__ __forceinline__ F ric_stage_elem(const F *scr, int N, int t, int e) {
+    using LY = RicLayout<NS, NU>;
+    constexpr int NX = NS + NU + 1, NG = NS * NX, NQ = NS * NS;
+    if (e < NG) {
+        const int k = e / NX, j = e % NX;
+        if (j < NS) return scr[LY::A(N, t) + k * NS + j];
+        if (j < NS + NU) return scr[LY::B(N, t) + k * NU + (j - NS)];
+        return scr[LY::c(N, t) + k];
+    }
+    if (e < NG + NQ) return scr[LY::Q(N, t) + (e - NG)];
+    if (e < NG + NQ + NS) return scr[LY::q(N, t) + (e - NG - NQ)];
+    return scr[LY::r(N, t) + (e - NG - NQ - NS)];
+}
+
+// inverse of a symmetric positive-definite n x n matrix (n <= 4), in registers
+template <typename F, int NU>
+__device__ __forceinline__ bool spd_inverse(const F (&U)[NU][NU], F (&X)[NU][NU]) {
+    if constexpr (NU == 2) {
+        const F det = U[0][0] * U[1][1] - U[0][1] * U[0][1];
+        if (!(U[0][0] > F(0)) || !(det > F(0))) return false;
+        const F id = F(1) / det;
+        X[0][0] = U[1][1] * id;
+        X[1][1] = U[0][0] * id;
+        X[0][1] = X[1][0] = -U[0][1] * id;
+        return true;
+    } else {
+        // Cholesky U = L L^T with reciprocal diagonal, then X = L^-T L^-1
+        F L[NU][NU], il[NU];
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < NU; ++c) {
+            F dg = U[c][c];
+#pragma unroll
+            for (int k = 0; k < c; ++k) dg -= L[c][k] * L[c][k];
+            ok &= dg > F(0);
+            dg = dg > F(0) ? dg : F(1);
+            const F sq = m_sqrt(dg);
+            il[c] = F(1) / sq;
+            L[c][c] = sq;
+#pragma unroll
+            for (int r = c + 1; r < NU; ++r) {
+                F acc = U[r][c];
+#pragma unroll
+                for (int k = 0; k < c; ++k) acc -= L[r][k] * L[c][k];
+                L[r][c] = acc * il[c];
+            }
+        }
+        // Z = L^-1 (lower triangular)
+        F Z[NU][NU];
+#pragma unroll
+        for (int c = 0; c < NU; ++c)
+#pragma unroll
+            for (int r = 0; r < NU; ++r) {
+                if (r < c) {
+                    Z[r][c] = F(0);
+                } else if (r == c) {
+                    Z[r][c] = il[r];
+                } else {
+                    F acc = F(0);
+#pragma unroll
+                    for (int k = c; k < r; ++k) acc -= L[r][k] * Z[k][c];
+                    Z[r][c] = acc * il[r];
+                }
+            }
+#pragma unroll
+        for (int i = 0; i < NU; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                F acc = F(0);
+#pragma unroll
+                for (int k = 0; k < NU; ++k) acc += Z[k][i] * Z[k][j];
+                X[i][j] = X[j][i] = acc;
+            }
+        return ok;
+    }
+}
+
+template <typename F, int NS, int NU>
 __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
     using LY = RicLayout<NS, NU>;
+    constexpr int NX = NS + NU + 1;           // columns of G = [A | B | c]
+    constexpr int NZ = NS + NU;               // rows of M
+    constexpr int MC = NZ + 1;                // columns of M as stored
+    constexpr int NG = NS * NX, NQ = NS * NS;
+    constexpr int NST = NG + NQ + NS + NU;    // staged values per step
+    constexpr int PF = (NST + 31) / 32;       // of them per lane
+    constexpr int NSYM = NZ * (NZ + 1) / 2;   // upper triangle of the Hessian part of M
+    constexpr int NPS = NS * (NS + 1) / 2;    // upper triangle of P
     const int lane = threadIdx.x;
-    __shared__ F P[NS * NS], pv[NS], PA[NS * NS], PB[NS * NU], wv[NS];
-    __shared__ F Quu[NU * NU], Qus[NU * NS], qu[NU], Qss[NS * NS], qs[NS], Kt[NU * NS], kt[NU];
-    __shared__ int bad;
-    if (lane == 0) bad = 0;
+    __shared__ F P[NS * NS], pv[NS], stg[NST], Y[NS * NX], M[NZ * MC], KK[NU * (NS + 1)];
+    const F *Gs = stg, *Qs = stg + NG, *qs = stg + NG + NQ, *rs = stg + NG + NQ + NS;
     for (int e = lane; e < NS * NS; e += 32) P[e] = scr[LY::Q(N, N) + e];
     for (int e = lane; e < NS; e += 32) pv[e] = scr[LY::q(N, N) + e];
-    __syncwarp();
+    F nxt[PF];
+    if (N >= 1) {
+#pragma unroll
+        for (int r = 0; r < PF; ++r) {
+            const int e = lane + 32 * r;
+            if (e < NST) nxt[r] = ric_stage_elem<F, NS, NU>(scr, N, N - 1, e);
+        }
+    }
+    bool ok = true;
     for (int t = N - 1; t >= 0; --t) {
-        const F *At = scr + LY::A(N, t), *Bt = scr + LY::B(N, t), *ct = scr + LY::c(N, t);
-        for (int e = lane; e < NS * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F acc = F(0);
-            for (int k = 0; k < NS; ++k) acc += P[i * NS + k] * At[k * NS + jj];
-            PA[e] = acc;
-        }
-        for (int e = lane; e < NS * NU; e += 32) {
-            const int i = e / NU, jj = e % NU;
-            F acc = F(0);
-            for (int k = 0; k < NS; ++k) acc += P[i * NS + k] * Bt[k * NU + jj];
-            PB[e] = acc;
-        }
-        for (int i = lane; i < NS; i += 32) {
-            F acc = pv[i];
-            for (int k = 0; k < NS; ++k) acc += P[i * NS + k] * ct[k];
-            wv[i] = acc;
+#pragma unroll
+        for (int r = 0; r < PF; ++r) {
+            const int e = lane + 32 * r;
+            if (e < NST) stg[e] = nxt[r];
         }
         __syncwarp();
-        const F *Qt = scr + LY::Q(N, t), *qt = scr + LY::q(N, t), *rt = scr + LY::r(N, t);
-        for (int e = lane; e < NS * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F acc = Qt[e];
-            for (int k = 0; k < NS; ++k) acc += At[k * NS + i] * PA[k * NS + jj];
-            Qss[e] = acc;
+        if (t >= 1) {
+#pragma unroll
+            for (int r = 0; r < PF; ++r) {
+                const int e = lane + 32 * r;
+                if (e < NST) nxt[r] = ric_stage_elem<F, NS, NU>(scr, N, t - 1, e);
+            }
         }
-        for (int e = lane; e < NU * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F acc = F(0);
-            for (int k = 0; k < NS; ++k) acc += Bt[k * NU + i] * PA[k * NS + jj];
-            Qus[e] = acc;
+        // Y = P G + [0 | 0 | p]
+        for (int e = lane; e < NS * NX; e += 32) {
+            const int k = e / NX, j = e % NX;
+            F acc = j == NX - 1 ? pv[k] : F(0);
+#pragma unroll
+            for (int l = 0; l < NS; ++l) acc += P[k * NS + l] * Gs[l * NX + j];
+            Y[e] = acc;
         }
-        for (int e = lane; e < NU * NU; e += 32) {
-            const int i = e / NU, jj = e % NU;
-            F acc = (i == jj) ? ru_diag[i] : F(0);
-            for (int k = 0; k < NS; ++k) acc += Bt[k * NU + i] * PB[k * NU + jj];
-            Quu[e] = acc;
-        }
-        for (int i = lane; i < NS + NU; i += 32) {
-            if (i < NS) {
-                F acc = qt[i];
-                for (int k = 0; k < NS; ++k) acc += At[k * NS + i] * wv[k];
-                qs[i] = acc;
+        __syncwarp();
+        // M: the upper triangle of the Hessian part, then the gradient column
+        for (int e = lane; e < NSYM + NZ; e += 32) {
+            int i, j;
+            if (e < NSYM) {
+                int rem = e;
+                i = 0;
+                while (rem >= NZ - i) {
+                    rem -= NZ - i;
+                    ++i;
+                }
+                j = i + rem;
             } else {
-                const int ii = i - NS;
-                F acc = rt[ii];
-                for (int k = 0; k < NS; ++k) acc += Bt[k * NU + ii] * wv[k];
-                qu[ii] = acc;
+                i = e - NSYM;
+                j = NZ;
             }
+            const int jy = j < NZ ? j : NX - 1;
+            F acc;
+            if (j == NZ) acc = i < NS ? qs[i] : rs[i - NS];
+            else if (j < NS) acc = Qs[i * NS + j];
+            else acc = (i == j) ? ru_diag[i - NS] : F(0);
+#pragma unroll
+            for (int k = 0; k < NS; ++k) acc += Gs[k * NX + i] * Y[k * NX + jy];
+            M[i * MC + j] = acc;
+            if (j < NZ && j != i) M[j * MC + i] = acc;
         }
         __syncwarp();
-        // Cholesky of Quu (NU <= 4) by lane 0
-        if (lane == 0) {
-            for (int c = 0; c < NU; ++c) {
-                F dg = Quu[c * NU + c];
-                for (int k = 0; k < c; ++k) dg -= Quu[c * NU + k] * Quu[c * NU + k];
-                if (!(dg > F(0))) {
-                    bad = 1;
-                    dg = F(1);
-                }
-                dg = m_sqrt(dg);
-                Quu[c * NU + c] = dg;
-                for (int r = c + 1; r < NU; ++r) {
-                    F acc = Quu[r * NU + c];
-                    for (int k = 0; k < c; ++k) acc -= Quu[r * NU + k] * Quu[c * NU + k];
-                    Quu[r * NU + c] = acc / dg;
-                }
-            }
+        // Quu^-1 (every lane), then [K_t | k_t] = -Quu^-1 [Qus | qu]
+        F U[NU][NU], X[NU][NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a)
+#pragma unroll
+            for (int b = 0; b < NU; ++b) U[a][b] = M[(NS + a) * MC + NS + b];
+        ok &= spd_inverse<F, NU>(U, X);
+        for (int e = lane; e < NU * (NS + 1); e += 32) {
+            const int a = e / (NS + 1), j = e % (NS + 1);
+            const int cj = j < NS ? j : NZ;
+            F acc = F(0);
+#pragma unroll
+            for (int b = 0; b < NU; ++b) acc -= X[a][b] * M[(NS + b) * MC + cj];
+            KK[e] = acc;
+            if (j < NS) scr[LY::K(N, t) + a * NS + j] = acc;
+            else scr[LY::k(N, t) + a] = acc;
         }
         __syncwarp();
-        // K = -Quu^-1 Qus (columns over lanes), k = -Quu^-1 qu (lane NS)
-        for (int col = lane; col <= NS; col += 32) {
-            F x[NU];
-            for (int i = 0; i < NU; ++i) x[i] = -(col < NS ? Qus[i * NS + col] : qu[i]);
-            for (int i = 0; i < NU; ++i) {
-                F acc = x[i];
-                for (int k = 0; k < i; ++k) acc -= Quu[i * NU + k] * x[k];
-                x[i] = acc / Quu[i * NU + i];
-            }
-            for (int i = NU - 1; i >= 0; --i) {
-                F acc = x[i];
-                for (int k = i + 1; k < NU; ++k) acc -= Quu[k * NU + i] * x[k];
-                x[i] = acc / Quu[i * NU + i];
-            }
-            for (int i = 0; i < NU; ++i) {
-                if (col < NS) {
-                    Kt[i * NS + col] = x[i];
-                    scr[LY::K(N, t) + i * NS + col] = x[i];
-                } else {
-                    kt[i] = x[i];
-                    scr[LY::k(N, t) + i] = x[i];
+        // P_t = Qss + Qus^T K_t (upper triangle, mirrored), p_t = qs + Qus^T k_t
+        for (int e = lane; e < NPS + NS; e += 32) {
+            if (e < NPS) {
+                int rem = e, i = 0;
+                while (rem >= NS - i) {
+                    rem -= NS - i;
+                    ++i;
                 }
+                const int j = i + rem;
+                F acc = M[i * MC + j];
+#pragma unroll
+                for (int a = 0; a < NU; ++a) acc += M[(NS + a) * MC + i] * KK[a * (NS + 1) + j];
+                P[i * NS + j] = acc;
+                P[j * NS + i] = acc;
+            } else {
+                const int i = e - NPS;
+                F acc = M[i * MC + NZ];
+#pragma unroll
+                for (int a = 0; a < NU; ++a) acc += M[(NS + a) * MC + i] * KK[a * (NS + 1) + NS];
+                pv[i] = acc;
             }
-        }
-        __syncwarp();
-        // P = Qss + Qus^T K (symmetrised), p = qs + Qus^T k
-        for (int e = lane; e < NS * NS; e += 32) {
-            const int i = e / NS, jj = e % NS;
-            F a1 = Qss[i * NS + jj], a2 = Qss[jj * NS + i];
-            for (int k = 0; k < NU; ++k) {
-                a1 += Qus[k * NS + i] * Kt[k * NS + jj];
-                a2 += Qus[k * NS + jj] * Kt[k * NS + i];
-            }
-            P[e] = F(0.5) * (a1 + a2);
-        }
-        for (int i = lane; i < NS; i += 32) {
-            F acc = qs[i];
-            for (int k = 0; k < NU; ++k) acc += Qus[k * NS + i] * kt[k];
-            pv[i] = acc;
         }
         __syncwarp();
     }
-    const int b = bad;
-    __syncwarp();
-    return b == 0;
+    return __all_sync(0xffffffffu, ok);
 }
 
 // Forward sweep u_t = K_t s_t + k_t, s_{t+1} = A_t s_t + B_t u_t + c_t from
