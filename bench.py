@@ -136,6 +136,9 @@ def gpu_arm(args):
     s0, u0, y0 = pb.s.clone(), pb.u.clone(), pb.y.clone()
     params = dict(binding.DEFAULTS)
     params["max_iter"] = args.max_iter
+    for k in ("prox", "damp"):
+        if getattr(args, k) is not None:
+            params[k] = getattr(args, k)
     if args.riccati_f32:
         params["flags"] = binding.OCA_ADMM_RICCATI_F32
 
@@ -373,6 +376,9 @@ def reference_arm(args):
     scene = synth.config3(n_scen=S)
     params = dict(binding.DEFAULTS)
     params["max_iter"] = args.max_iter
+    for k in ("prox", "damp"):
+        if getattr(args, k) is not None:
+            params[k] = getattr(args, k)
     kw = {k: params[k] for k in ("sigma", "eps_pri", "eps_dual", "prox", "max_iter", "rho_box", "damp")}
     per_step = max(1, cores)
 
@@ -417,6 +423,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warps", type=int, default=0, help="warps per tile (0: autotune)")
     ap.add_argument("--riccati-f32", action="store_true", help="factorise the trajectory QP in FP32")
+    ap.add_argument("--prox", type=float, default=None, help="proximal weight of the pair QP (default: library default)")
+    ap.add_argument("--damp", type=float, default=None, help="proximal damping of the trajectory step")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

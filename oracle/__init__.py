@@ -266,7 +266,7 @@ def pair_qp_batch(scene, states, zeta, xi, y_in, prox: float = 0.0, pairs=None, 
     return dict(y=y_out, v=v, obj=obj, status=status)
 
 
-def admm_batch(scene, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.1, max_iter=300,
+def admm_batch(scene, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1.0, max_iter=300,
                jacobi=False, scenarios=None, s=None, u=None, y=None, zeta=None, xi=None,
                nthreads: int = 0, rho_box=100.0, damp=100.0):
     """Whole ADMM solves; returns the updated state arrays and the report."""

@@ -299,10 +299,10 @@ def pair_qp(ds: DeviceScene, states, zeta, xi, y_in, prox: float = 0.0, y_out=No
     return dict(y=y_out, v=v, obj=obj, status=status)
 
 
-DEFAULTS = dict(sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.1, max_iter=300, rho_box=100.0, damp=100.0)
+DEFAULTS = dict(sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1.0, max_iter=300, rho_box=100.0, damp=100.0)
 
 
-def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=0.1,
+def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1.0,
                max_iter=300, flags=0, rho_box=100.0, damp=100.0, stream=None, tape=None):
     """oca_admm_solve (oca_admm_solve_taped when `tape` is given): updates s,
     u, y, zeta, xi in place; returns the report."""
@@ -338,7 +338,7 @@ def new_tape(ds: DeviceScene, max_iter: int) -> torch.Tensor:
     return torch.empty(tape_bytes(ds, max_iter), dtype=torch.uint8, device=ds.device)
 
 
-def admm_backward(ds: DeviceScene, s_ref, tape, iters, grad_cost, grad_alpha=None, sigma=300.0, prox=0.1,
+def admm_backward(ds: DeviceScene, s_ref, tape, iters, grad_cost, grad_alpha=None, sigma=300.0, prox=1.0,
                   max_iter=300, rho_box=100.0, damp=100.0, eps_pri=1e-4, eps_dual=1e-4, flags=0, stream=None):
     """oca_admm_backward: gradients of sum_s grad_cost[s] * cost_s (+ sum_p
     grad_alpha[p] * alpha*_p at the returned trajectory) of a taped solve
