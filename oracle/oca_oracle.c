@@ -945,7 +945,14 @@ int ora_admm_scenario(const ora_model *md, const ora_scene *sc, int scen, const 
                 qt[a] += g[a] - hs;                 /* linear term of 0.5|r0 + J (s - sbar)|^2 */
             }
         }
-        if (ora_riccati(ns, nu, N, Aq, Bq, cq, Qq, qq, Rq, rq, s, sn, un) != ORA_OK) {
+        int finite = 1;
+        if (ora_riccati(ns, nu, N, Aq, Bq, cq, Qq, qq, Rq, rq, s, sn, un) == ORA_OK) {
+            for (int k = 0; k < (N + 1) * ns; ++k) finite &= isfinite(sn[k]) != 0;
+            for (int k = 0; k < N * nu; ++k) finite &= isfinite(un[k]) != 0;
+        } else {
+            finite = 0;
+        }
+        if (!finite) {  /* singular or non-finite trajectory step: the iteration has diverged */
             status = ORA_FAIL;
             break;
         }

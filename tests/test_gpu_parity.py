@@ -157,6 +157,7 @@ def test_pair_qp_prox0_parity(B, ctx, ora, name, dtype, warm):
 
 @pytest.mark.parametrize("name,dtype,prox", [("c1", F64, 0.1), ("c1", F32, 0.1), ("c2", F32, 1e-2),
                                              ("c2", F32, 0.1), ("c3", F32, 0.1), ("c3", F32, 1e-2),
+                                             ("c1", F64, 1.0), ("c3", F32, 1.0), ("c4", F32, 1.0),
                                              ("c4", F32, 0.1), ("c4", F64, 0.1)])
 def test_pair_qp_prox_parity(B, ctx, ora, name, dtype, prox):
     """prox > 0: the solution is unique; y, v and objective agree.  Pairs the
@@ -228,6 +229,18 @@ def test_admm_fixed_iterations_fp64(B, ctx, ora, kw):
     assert int(rep["status"][0]) == 1 and int(rep["iters"][0]) == 7 and ref["iters"][0] == 7
     assert np.abs(pb.s.cpu().numpy() - ref["s"]).max() < 1e-8
     assert np.abs(pb.xi.cpu().numpy().T - ref["xi"]).max() < 1e-8
+
+
+@pytest.mark.parametrize("name", ["c2", "c4"])
+def test_admm_fixed_iterations_fp64_models(B, ctx, ora, name):
+    """Trailer (two parts, hinge state) and quadrotor (3-D, three boxes):
+    10 iterations without the stopping test agree iterate for iterate."""
+    sc = _scene(name)
+    ds, pb, rep, ref = _admm_both(B, ctx, ora, sc, F64, max_iter=10, eps_pri=0.0, eps_dual=0.0)
+    assert (rep["iters"].cpu().numpy() == 10).all() and (ref["iters"] == 10).all()
+    assert np.abs(pb.s.cpu().numpy() - ref["s"]).max() < 1e-7 * (1 + np.abs(ref["s"]).max())
+    assert np.abs(pb.u.cpu().numpy() - ref["u"]).max() < 1e-7 * (1 + np.abs(ref["u"]).max())
+    assert np.abs(pb.zeta.cpu().numpy() - ref["zeta"]).max() < 1e-7 * (1 + np.abs(ref["zeta"]).max())
 
 
 @pytest.mark.parametrize("name", ["c2", "c3", "c5"])
