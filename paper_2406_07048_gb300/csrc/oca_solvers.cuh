@@ -1052,10 +1052,47 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
 template <typename T, int D, int NR>
 OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T bq[D + 1], T w[D + 1],
                                    SsnEval<T, D, NR> &st) {
+    // One loop with a single evaluation site: every pass evaluates y(w) at
+    // one point -- the start point, or a trial w + t d of the line search --
+    // and then either backtracks, or accepts the trial and computes the next
+    // Newton direction.  (The same sequence of evaluations as a Newton loop
+    // with a nested line search; but the large evaluation code exists once,
+    // and lanes of a warp in different phases share evaluation passes.)
     constexpr int V = D + 1;
-    ssn_eval_staged<T, D, NR>(L, rho_p, bq, w, st);
     int status = OCA_PAIR_ITER_CAP;
-    for (int it = 0; it < 60; ++it) {
+    T dlt[V], wt[V], tstep = T(1), gd = T(0);
+    bool started = false;
+    int it = 0, ls = 0;
+    for (int pass = 0; pass < 1 + 60 * 30; ++pass) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) wt[i] = started ? w[i] + tstep * dlt[i] : w[i];
+        SsnEval<T, D, NR> trial;
+        ssn_eval_staged<T, D, NR>(L, rho_p, bq, wt, trial);
+        if (started) {
+            const bool ok = trial.psi <= st.psi + T(1e-4) * tstep * gd + T(8) * m_eps<T>() * (st.pmag + trial.pmag);
+            if (!ok && ls < 29) {
+                // backtracking on psi: psi is piecewise quadratic along the ray,
+                // so the minimiser of the quadratic through psi(0), psi'(0) = gd
+                // and psi(t) is usually exact after one rejected trial
+                const T curv = trial.psi - st.psi - tstep * gd;   // (psi(t) - psi(0) - t psi'(0)) = a t^2
+                T tn = curv > T(0) ? -gd * tstep * tstep / (T(2) * curv) : T(0.5) * tstep;
+                tstep = fmin(fmax(tn, T(0.1) * tstep), T(0.5) * tstep);
+                ++ls;
+                continue;
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i) w[i] = wt[i];
+            st = trial;
+            if (!ok) {
+                status = OCA_PAIR_OK;  // no decrease at rounding level
+                break;
+            }
+            if (++it >= 60) break;
+        } else {
+            st = trial;
+            started = true;
+        }
+        // convergence test and the next Newton direction at w
         T F[V], fn = T(0), scale = T(1) + st.mag;
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -1071,7 +1108,7 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
             status = OCA_PAIR_NONFINITE;
             break;
         }
-        T G[V][V], dlt[V];
+        T G[V][V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             dlt[i] = -rho_p * F[i];
@@ -1082,7 +1119,7 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
 #pragma unroll
             for (int i = 0; i < V; ++i) dlt[i] = -F[i];
         }
-        T gd = T(0);
+        gd = T(0);
 #pragma unroll
         for (int i = 0; i < V; ++i) gd += F[i] * dlt[i];
         if (!(gd < T(0))) {
@@ -1092,32 +1129,8 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
 #pragma unroll
             for (int i = 0; i < V; ++i) gd -= F[i] * F[i];
         }
-        // backtracking on psi: psi is piecewise quadratic along the ray, so the
-        // minimiser of the quadratic through psi(0), psi'(0) = gd and psi(t)
-        // is usually exact after one rejected trial
-        T tstep = T(1);
-        SsnEval<T, D, NR> trial;
-        T wt[V];
-        bool ok = false;
-        for (int ls = 0; ls < 30; ++ls) {
-#pragma unroll
-            for (int i = 0; i < V; ++i) wt[i] = w[i] + tstep * dlt[i];
-            ssn_eval_staged<T, D, NR>(L, rho_p, bq, wt, trial);
-            if (trial.psi <= st.psi + T(1e-4) * tstep * gd + T(8) * m_eps<T>() * (st.pmag + trial.pmag)) {
-                ok = true;
-                break;
-            }
-            const T curv = trial.psi - st.psi - tstep * gd;   // (psi(t) - psi(0) - t psi'(0)) = a t^2
-            T tn = curv > T(0) ? -gd * tstep * tstep / (T(2) * curv) : T(0.5) * tstep;
-            tstep = fmin(fmax(tn, T(0.1) * tstep), T(0.5) * tstep);
-        }
-#pragma unroll
-        for (int i = 0; i < V; ++i) w[i] = wt[i];
-        st = trial;
-        if (!ok) {
-            status = OCA_PAIR_OK;  // no decrease at rounding level
-            break;
-        }
+        tstep = T(1);
+        ls = 0;
     }
     return status;
 }
