@@ -291,6 +291,43 @@ oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_mod
                              const int32_t *iters, const void *grad_cost, const void *grad_alpha,
                              void *grad_obs_offset, void *grad_obs_center, void *grad_state0, void *stream);
 /* ------------------------------------------------------------------------ */
+/* Closed-loop receding-horizon control                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_steps;   /* control steps C >= 1                                        */
+    int32_t reserved;  /* 0                                                           */
+    double window[3];  /* sensing box half-widths around the position (Sec. V-B senses
+                          20 x 20 x 6 m: 10, 10, 3); <= 0 leaves an axis unlimited      */
+} oca_mpc_params;
+/* The paper's closed loop (Sec. V-B), every scenario at once.  Per control
+ * step c = 0..C-1:
+ *   1. the horizon window: s_ref rows t = 0..N <- ref[c + t] (clamped to the
+ *      last row); for c > 0 the warm start is shifted one step (s_t <- s_{t+1},
+ *      u_t <- u_{t+1}, and y, zeta, xi of pair (j, part, t) <- (j, part, t+1));
+ *      s_0 <- the true state;
+ *   2. the sensing cull: obstacles whose centre lies outside the box
+ *      |centre - position| <= window take no part in this step's solve (their
+ *      pairs keep y, zeta, xi);
+ *   3. the ADMM of oca_admm_solve with `params`;
+ *   4. the plant: x <- x + dt f_c(x, u_0), u_0 the plan's first control clipped
+ *      to the control box (0 where non-finite);
+ *   5. collision of the true state with every obstacle (alpha* < 1 of the
+ *      scale LP, sensed or not).
+ * ref        [S][T_ref][ns] device: the reference state of every control step.
+ * obs_center [M_tot][dim] device: the point the sensing window tests.
+ * x          [S][ns] device in/out: the true state.
+ * s_ref, s, u, y, zeta, xi: as for oca_admm_solve (in: the first warm start,
+ *            out: the last window and plan).
+ * x_hist [S][C+1][ns], u_hist [S][C][nu] (scene dtype), iters_hist [S][C],
+ * collided [S] (int32; the first control step whose true state collides, -1
+ * if none) out.
+ * Synchronous with the host between control steps (the ADMM's chunk checks).
+ * Errors: OCA_ERR_INVALID_ARGUMENT, OCA_ERR_CUDA. */
+oca_status oca_mpc_run(oca_ctx *ctx, const oca_scene *scene, const oca_model *model, const oca_admm_params *params,
+                       const oca_mpc_params *mpc, const void *ref, int32_t T_ref, const void *obs_center, void *x,
+                       void *s_ref, void *s, void *u, void *y, void *zeta, void *xi, void *x_hist, void *u_hist,
+                       int32_t *iters_hist, int32_t *collided, void *stream);
+/* ------------------------------------------------------------------------ */
 /* Collision detection without allocation                                   */
 /* ------------------------------------------------------------------------ */
 

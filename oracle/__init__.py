@@ -2,8 +2,9 @@
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The arithmetic lives in
-``oca_oracle.c`` (plain C, FP64); this file only compiles it with gcc and
-marshals numpy arrays.  It shares nothing with the CUDA path.
+``oca_oracle.c`` (plain C, FP64); this file compiles it with gcc, marshals
+numpy arrays, and composes the closed loop (``mpc_run``) from those routines.
+It shares nothing with the CUDA path.
 """
 from __future__ import annotations
 
@@ -291,3 +292,108 @@ def admm_batch(scene, sigma=300.0, eps_pri=1e-4, eps_dual=1e-4, prox=1.0, max_it
 
 def num_threads() -> int:
     return int(lib().ora_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# closed-loop receding-horizon control (Sec. V-B), composed from the routines
+# above; kept in Python because it is bookkeeping around them
+# ---------------------------------------------------------------------------
+
+def _sensed_subscene(scene, keep):
+    """The scene restricted to the obstacles with keep[j] (scenario structure,
+    parts and states unchanged) and, for every scenario, the indices of its
+    kept pairs in the full scene (obstacle-major blocks, kept in order)."""
+    import dataclasses
+    keep = np.asarray(keep, bool)
+    ob = np.asarray(scene.obs_begin)
+    counts = [int(keep[ob[s]:ob[s + 1]].sum()) for s in range(scene.n_scen)]
+    sub = dataclasses.replace(scene, obs_C=scene.obs_C[keep], obs_d=scene.obs_d[keep], obs_nf=scene.obs_nf[keep],
+                              obs_center=scene.obs_center[keep], obs_off=scene.obs_off[keep],
+                              obs_begin=np.concatenate([[0], np.cumsum(counts)]).astype(np.int32))
+    idx = []
+    for s in range(scene.n_scen):
+        N, NP = int(scene.horizon[s]), scene.n_parts(s)
+        for j in range(scene.n_obs(s)):
+            if keep[ob[s] + j]:
+                p0 = int(scene.pair_begin[s]) + j * NP * N
+                idx.append(np.arange(p0, p0 + NP * N))
+    idx = np.concatenate(idx) if idx else np.zeros(0, np.int64)
+    return sub, idx
+
+
+def mpc_run(scene, ref, x0, n_steps, window=(10.0, 10.0, 3.0), s_init=None, nthreads: int = 0, **admm):
+    """The closed loop of every scenario (same steps as the GPU's
+    oca_mpc_run): per control step the horizon window of the reference, the
+    warm start shifted one step, s_0 = the true state, the ADMM over the
+    sensed obstacles only (admm_batch on the sub-scene; the other pairs keep
+    y, zeta, xi), the plant x += dt f_c(x, u_0) with u_0 clipped to the
+    control box, and the collision test alpha* < 1 against every obstacle."""
+    sc = scene
+    S, ns, nu, d = sc.n_scen, sc.model.ns, sc.model.nu, sc.dim
+    ref = np.asarray(ref, np.float64)
+    T_ref = ref.shape[1]
+    s = np.array(sc.s_init if s_init is None else s_init, np.float64)
+    u = np.array(sc.u_init, np.float64)
+    s_ref = np.array(sc.s_ref, np.float64)
+    y = sc.cold_y().astype(np.float64)
+    zeta = np.zeros(sc.n_pairs)
+    xi = np.zeros((sc.n_pairs, d))
+    x = np.array(x0, np.float64)
+    x_hist = np.zeros((S, n_steps + 1, ns))
+    u_hist = np.zeros((S, n_steps, nu))
+    it_hist = np.zeros((S, n_steps), np.int32)
+    collided = np.full(S, -1, np.int32)
+    x_hist[:, 0] = x
+    win = np.asarray(window, np.float64)
+    for c in range(n_steps):
+        keep = np.zeros(len(sc.obs_nf), bool)
+        for si in range(S):
+            N, a, b = int(sc.horizon[si]), int(sc.state_begin[si]), int(sc.ctrl_begin[si])
+            for t in range(N + 1):
+                s_ref[a + t] = ref[si, min(c + t, T_ref - 1)]
+            if c > 0:
+                s[a + 1:a + N] = s[a + 2:a + N + 1].copy()
+                u[b:b + N - 1] = u[b + 1:b + N].copy()
+                NP = sc.n_parts(si)
+                for blk in range(sc.n_obs(si) * NP):
+                    p0 = int(sc.pair_begin[si]) + blk * N
+                    y[p0:p0 + N - 1] = y[p0 + 1:p0 + N].copy()
+                    zeta[p0:p0 + N - 1] = zeta[p0 + 1:p0 + N].copy()
+                    xi[p0:p0 + N - 1] = xi[p0 + 1:p0 + N].copy()
+            s[a] = x[si]
+            for j in range(sc.n_obs(si)):
+                gm = int(sc.obs_begin[si]) + j
+                inside = True
+                for i in range(d):
+                    if win[i] > 0:
+                        inside &= abs(sc.obs_center[gm, i] - x[si, i]) <= win[i]
+                keep[gm] = inside
+        sub, idx = _sensed_subscene(sc, keep)
+        import dataclasses
+        sub = dataclasses.replace(sub, s_ref=s_ref.copy())
+        r = admm_batch(sub, s=s, u=u, y=y[idx], zeta=zeta[idx], xi=xi[idx], nthreads=nthreads, **admm)
+        y[idx], zeta[idx], xi[idx] = r["y"], r["zeta"], r["xi"]
+        s, u = r["s"], r["u"]
+        it_hist[:, c] = r["iters"]
+        m = sc.model
+        for si in range(S):
+            b = int(sc.ctrl_begin[si])
+            u0 = np.where(np.isfinite(u[b]), u[b], 0.0)
+            u0 = np.minimum(np.maximum(u0, m.u_lo), m.u_hi)
+            f = dynamics(m, x[si], u0)[0]
+            x[si] = x[si] + m.dt * f
+            u_hist[si, c] = u0
+            x_hist[si, c + 1] = x[si]
+            for part in range(sc.n_parts(si)):
+                gp = int(sc.part_begin[si]) + part
+                rho, R, _, _ = part_pose(m, int(sc.part_link[gp]), sc.part_off[gp], x[si])
+                nr = int(sc.part_nf[gp])
+                for j in range(sc.n_obs(si)):
+                    gm = int(sc.obs_begin[si]) + j
+                    nf = int(sc.obs_nf[gm])
+                    Cw, dw = sc.obs_C[gm, :nf], sc.obs_d[gm, :nf]
+                    al = scale_lp(sc.part_A[gp, :nr], sc.part_b[gp, :nr], Cw @ R, dw - Cw @ rho)[0]
+                    if al < 1.0 and collided[si] < 0:
+                        collided[si] = c + 1
+    return dict(x=x, x_hist=x_hist, u_hist=u_hist, iters=it_hist, collided=collided, s=s, u=u, y=y, zeta=zeta,
+                xi=xi, s_ref=s_ref)

@@ -62,6 +62,10 @@ class ProfileStats(C.Structure):
                 ("traj_launches", C.c_int64)]
 
 
+class MpcParams(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("reserved", C.c_int32), ("window", C.c_double * 3)]
+
+
 class Report(C.Structure):
     _fields_ = [("iters", C.c_void_p), ("status", C.c_void_p), ("r_pri", C.c_void_p), ("r_dual", C.c_void_p),
                 ("cost", C.c_void_p)]
@@ -70,7 +74,8 @@ class Report(C.Structure):
 EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create", "oca_scene_destroy",
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
             "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
-            "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward"]
+            "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward",
+            "oca_mpc_run"]
 
 
 def lib():
@@ -118,6 +123,9 @@ def lib():
         L.oca_admm_backward.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, C.c_int64, P, P, P,
                                         P, P, P, P]
         L.oca_admm_backward.restype = I
+        L.oca_mpc_run.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), C.POINTER(MpcParams), P, I, P, P,
+                                  P, P, P, P, P, P, P, P, P, P, P]
+        L.oca_mpc_run.restype = I
         _lib = L
     return _lib
 
@@ -414,3 +422,37 @@ class Problem:
 
     def solve(self, **kw):
         return admm_solve(self.ds, self.s_ref, self.s, self.u, self.y, self.zeta, self.xi, **kw)
+
+
+def mpc_run(ds: DeviceScene, ref, obs_center, x0, n_steps: int, window=(10.0, 10.0, 3.0), s_init=None, stream=None,
+            **admm):
+    """oca_mpc_run: the closed loop of every scenario for n_steps control
+    steps from the true states x0 [S, ns], with the scene's first window as
+    the first warm start.  Returns the histories, iteration counts, the
+    first colliding step per scenario (-1: none) and the final arrays."""
+    sc = ds.scene
+    S, ns, nu = sc.n_scen, sc.model.ns, sc.model.nu
+    kw = dict(DEFAULTS)
+    kw.update(admm)
+    pr = AdmmParams(float(kw["sigma"]), float(kw["eps_pri"]), float(kw["eps_dual"]), float(kw["prox"]),
+                    int(kw["max_iter"]), int(kw.get("flags", 0)), float(kw["rho_box"]), float(kw["damp"]))
+    mp = MpcParams(int(n_steps), 0, (C.c_double * 3)(*[float(w) for w in window]))
+    ref_t = ds.tensor(ref)
+    ctr = ds.tensor(obs_center)
+    x = ds.tensor(x0)
+    s_ref = ds.tensor(sc.s_ref)
+    s = ds.tensor(sc.s_init if s_init is None else s_init)
+    u = ds.tensor(sc.u_init)
+    y = ds.to_device_pairs(sc.cold_y())
+    zeta = torch.zeros(ds.n_pairs, dtype=ds.dtype, device=ds.device)
+    xi = torch.zeros(sc.dim, ds.n_pairs, dtype=ds.dtype, device=ds.device)
+    x_hist = torch.zeros(S, n_steps + 1, ns, dtype=ds.dtype, device=ds.device)
+    u_hist = torch.zeros(S, n_steps, nu, dtype=ds.dtype, device=ds.device)
+    it_hist = torch.zeros(S, n_steps, dtype=torch.int32, device=ds.device)
+    coll = torch.zeros(S, dtype=torch.int32, device=ds.device)
+    _check(lib().oca_mpc_run(ds.ctx.h, ds.h, C.byref(ds.model), C.byref(pr), C.byref(mp), _ptr(ref_t),
+                             int(ref_t.shape[1]), _ptr(ctr), _ptr(x), _ptr(s_ref), _ptr(s), _ptr(u), _ptr(y),
+                             _ptr(zeta), _ptr(xi), _ptr(x_hist), _ptr(u_hist), _ptr(it_hist), _ptr(coll),
+                             _stream(stream)), "oca_mpc_run")
+    return dict(x=x, x_hist=x_hist, u_hist=u_hist, iters=it_hist, collided=coll, s=s, u=u, y=y, zeta=zeta, xi=xi,
+                s_ref=s_ref)

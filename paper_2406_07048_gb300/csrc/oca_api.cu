@@ -41,6 +41,9 @@ struct oca_scene {
     long long *d_ric_off = nullptr;
     int *d_status = nullptr, *d_iter = nullptr, *d_active = nullptr, *d_err = nullptr;
     void *d_box = nullptr;      // z_s, w_s [n_states][NSmax]; z_u, w_u [n_ctrls][NUmax]
+    int *d_mpc_i = nullptr;     // closed loop: per-step report (iters, status) [2][S]
+    double *d_mpc_f = nullptr;  // per-step report (r_pri, r_dual, cost) [3][S] (scene dtype)
+    unsigned char *d_mask = nullptr;  // [M_tot] sensed obstacles
     double *d_box_res = nullptr;  // [S][2]
     int ns_max = 0, nu_max = 0;
     int *h_active = nullptr;
@@ -354,7 +357,7 @@ __global__ void k_cast_d2t(const double *x, long long n, T *y) {
 template <typename T>
 oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *s,
                      void *u, void *y, void *zeta, void *xi, const oca_admm_report *rep, cudaStream_t st,
-                     void *tape = nullptr) {
+                     void *tape = nullptr, const unsigned char *obs_mask = nullptr) {
     k_reset<<<(sc->S + 255) / 256, 256, 0, st>>>(sc->d_status, sc->S, sc->d_iter, sc->d_active);
     OCA_CK(cudaGetLastError());
     const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
@@ -417,6 +420,7 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     a.iter = sc->d_iter;
     a.max_iter = pr->max_iter;
     a.prox = T(pr->prox);
+    a.obs_mask = obs_mask;
     const int solver = pr->prox > 0.0 ? 1 : 0;
 
     RicArgs<T> r;
@@ -680,6 +684,60 @@ oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_param
     return OCA_OK;
 }
 
+
+template <typename T>
+oca_status mpc_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const oca_mpc_params *mp,
+                    const void *ref, int T_ref, const void *obs_center, void *x, void *s_ref, void *s, void *u,
+                    void *y, void *zeta, void *xi, void *x_hist, void *u_hist, int32_t *iters_hist,
+                    int32_t *collided, cudaStream_t st) {
+    MpcArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.meta = sc->d_meta;
+    a.g = make_geom<T>(sc);
+    a.model = make_model<T>(m);
+    a.ref = static_cast<const T *>(ref);
+    a.T_ref = T_ref;
+    a.obs_center = static_cast<const T *>(obs_center);
+    for (int i = 0; i < 3; ++i) a.win[i] = T(mp->window[i]);
+    a.x = static_cast<T *>(x);
+    a.s = static_cast<T *>(s);
+    a.u = static_cast<T *>(u);
+    a.s_ref = static_cast<T *>(s_ref);
+    a.y = static_cast<T *>(y);
+    a.zeta = static_cast<T *>(zeta);
+    a.xi = static_cast<T *>(xi);
+    a.P = sc->P;
+    a.FR = sc->FR;
+    a.FO = sc->FO;
+    a.mask = sc->d_mask;
+    a.x_hist = static_cast<T *>(x_hist);
+    a.u_hist = static_cast<T *>(u_hist);
+    a.n_steps = mp->n_steps;
+    a.collided = collided;
+    a.iters_hist = iters_hist;
+    a.iters = sc->d_mpc_i;
+    oca_admm_report rep;
+    rep.iters = sc->d_mpc_i;
+    rep.status = sc->d_mpc_i + sc->S;
+    T *rf = reinterpret_cast<T *>(sc->d_mpc_f);
+    rep.r_pri = rf;
+    rep.r_dual = rf + sc->S;
+    rep.cost = rf + 2 * sc->S;
+    int max_blk = 1;
+    for (const ScenMeta &m2 : sc->meta) max_blk = std::max(max_blk, m2.M * m2.NP);
+    OCA_CK(cudaMemsetAsync(collided, 0xff, sizeof(int32_t) * sc->S, st));
+    for (int c = 0; c < mp->n_steps; ++c) {
+        a.c = c;
+        OCA_CK(launch_mpc<T>(a, 0, sc->S, max_blk, st));
+        if (c > 0) OCA_CK(launch_mpc<T>(a, 1, sc->S, max_blk, st));
+        const oca_status e = admm_impl<T>(sc, m, pr, s_ref, s, u, y, zeta, xi, &rep, st, nullptr, sc->d_mask);
+        if (e != OCA_OK) return e;
+        OCA_CK(launch_mpc<T>(a, 2, sc->S, max_blk, st));
+        OCA_CK(launch_mpc<T>(a, 3, sc->S, max_blk, st));
+    }
+    return OCA_OK;
+}
+
 void free_scene(oca_scene *sc) {
     if (!sc) return;
     cudaFree(sc->d_meta);
@@ -695,6 +753,9 @@ void free_scene(oca_scene *sc) {
     cudaFree(sc->d_res);
     cudaFree(sc->d_ric_off);
     cudaFree(sc->d_status);
+    cudaFree(sc->d_mpc_i);
+    cudaFree(sc->d_mpc_f);
+    cudaFree(sc->d_mask);
     cudaFree(sc->d_iter);
     cudaFree(sc->d_active);
     cudaFree(sc->d_err);
@@ -900,6 +961,9 @@ oca_status oca_scene_create(oca_ctx *ctx, const oca_scene_desc *d, oca_scene **o
         (e = dmalloc(&sc->d_ric_off, sizeof(long long) * S)) != OCA_OK ||
         (e = dmalloc(&sc->d_res, sizeof(double) * 4 * (size_t)tiles)) != OCA_OK ||
         (e = dmalloc(&sc->d_status, sizeof(int) * S)) != OCA_OK ||
+        (e = dmalloc(&sc->d_mpc_i, sizeof(int) * 2 * S)) != OCA_OK ||
+        (e = dmalloc(&sc->d_mpc_f, sizeof(double) * 3 * S)) != OCA_OK ||
+        (e = dmalloc(&sc->d_mask, (size_t)M_tot)) != OCA_OK ||
         (e = dmalloc(&sc->d_iter, sizeof(int))) != OCA_OK ||
         (e = dmalloc(&sc->d_active, sizeof(int))) != OCA_OK ||
         (e = dmalloc(&sc->d_err, sizeof(int))) != OCA_OK ||
@@ -1075,6 +1139,31 @@ oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_mod
                                     grad_obs_center, grad_state0, st);
     return backward_impl<double>(sc, model, params, s_ref, tape, iters, grad_cost, grad_alpha, grad_obs_offset,
                                  grad_obs_center, grad_state0, st);
+}
+
+
+oca_status oca_mpc_run(oca_ctx *ctx, const oca_scene *scene, const oca_model *model, const oca_admm_params *params,
+                       const oca_mpc_params *mpc, const void *ref, int32_t T_ref, const void *obs_center, void *x,
+                       void *s_ref, void *s, void *u, void *y, void *zeta, void *xi, void *x_hist, void *u_hist,
+                       int32_t *iters_hist, int32_t *collided, void *stream) {
+    if (!ctx || !scene || !params || !mpc || !ref || !obs_center || !x || !s_ref || !s || !u || !y || !zeta || !xi ||
+        !x_hist || !u_hist || !iters_hist || !collided)
+        return OCA_ERR_INVALID_ARGUMENT;
+    if (!(params->sigma > 0.0) || !(params->prox >= 0.0) || !(params->eps_pri >= 0.0) || !(params->eps_dual >= 0.0) ||
+        params->max_iter < 0 || !(params->rho_box >= 0.0) || !(params->damp >= 0.0))
+        return OCA_ERR_INVALID_ARGUMENT;
+    if (mpc->n_steps < 1 || T_ref < 1) return OCA_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < 3; ++i)
+        if (std::isnan(mpc->window[i])) return OCA_ERR_INVALID_ARGUMENT;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    const oca_status e = check_model(sc, model);
+    if (e != OCA_OK) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32)
+        return mpc_impl<float>(sc, model, params, mpc, ref, T_ref, obs_center, x, s_ref, s, u, y, zeta, xi, x_hist,
+                               u_hist, iters_hist, collided, st);
+    return mpc_impl<double>(sc, model, params, mpc, ref, T_ref, obs_center, x, s_ref, s, u, y, zeta, xi, x_hist,
+                            u_hist, iters_hist, collided, st);
 }
 
 }  // extern "C"

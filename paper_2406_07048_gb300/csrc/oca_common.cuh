@@ -132,6 +132,7 @@ struct PairArgs {
     const int *iter;        // ADMM mode: device iteration counter j
     int max_iter;
     T prox;
+    const unsigned char *obs_mask;  // [M_tot] or null: obstacles with 0 are skipped (their y passed through)
 };
 
 template <typename T>
@@ -246,6 +247,30 @@ struct AdjAlphaArgs {
     const T *grad_alpha;    // [P]
     T *poseb;               // [PK][Qtot] out: adjoint of those poses
     double *gd;             // [M_tot][FO] accumulated adjoint of the obstacle offsets
+};
+
+// closed-loop receding-horizon control (oca_mpc_run)
+template <typename T>
+struct MpcArgs {
+    const ScenMeta *meta;
+    Geom<T> g;
+    DevModel<T> model;
+    const T *ref;          // [S][T_ref][NS] reference of every control step
+    int T_ref;
+    const T *obs_center;   // [M_tot][D]
+    T win[3];              // sensing half-widths per axis (<= 0: no limit on that axis)
+    T *x;                  // [S][NS] true state
+    T *s, *u, *s_ref;      // the scene's state arrays (warm start, window)
+    T *y, *zeta, *xi;      // pair arrays
+    long long P;
+    int FR, FO;
+    unsigned char *mask;   // [M_tot] sensed obstacles of this step
+    T *x_hist, *u_hist;    // [S][n_steps + 1][NS], [S][n_steps][NU]
+    int n_steps;
+    int *collided;         // [S] first control step whose true state collides, or -1
+    int *iters_hist;       // [S][n_steps]
+    const int *iters;      // [S] iterations of this step's solve
+    int c;                 // control step
 };
 
 }  // namespace oca

@@ -30,6 +30,9 @@ template <typename T>
 cudaError_t launch_adj_alpha(const AdjAlphaArgs<T> &a, int dim, int n_tiles, int W, const int *iters,
                              const T *tape_s, long long s_slot, int NS, int n_scen, T *states_out,
                              const PoseArgs<T> &pa, int maxQ, cudaStream_t st);
+// closed loop (oca_mpc.cu): stage 0 window/shift/mask, 1 pair shift, 2 plant, 3 collision
+template <typename T>
+cudaError_t launch_mpc(const MpcArgs<T> &a, int stage, int n_scen, int max_blk, cudaStream_t st);
 template <typename T>
 cudaError_t launch_adj_finish(const double *gd, const T *obs_C, const int *obs_nf, int M_tot, int FO, int dim,
                               T *grad_d, T *grad_ctr, cudaStream_t st);

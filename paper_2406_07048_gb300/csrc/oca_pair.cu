@@ -155,6 +155,16 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
             L.no = a.g.obs_nf[gm];
             const long long p = sm.pair0 + (long long)j * Q + q;
             const int ng = L.nr + L.no + 1;
+            if (a.obs_mask && !a.obs_mask[gm]) {
+                // an obstacle outside the sensing window: its pairs take no
+                // part in this solve and keep their y in both buffers
+                if (y_out != y_in) {
+                    for (int k = 0; k < L.nr; ++k) y_out[(long long)k * P + p] = y_in[(long long)k * P + p];
+                    for (int m = 0; m < L.no; ++m) y_out[(long long)(FR + m) * P + p] = y_in[(long long)(FR + m) * P + p];
+                    y_out[(long long)(FR + FO) * P + p] = y_in[(long long)(FR + FO) * P + p];
+                }
+                continue;
+            }
             T zeta = a.zeta[p];
             T xi[D];
 #pragma unroll

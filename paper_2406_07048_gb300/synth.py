@@ -445,6 +445,46 @@ def config4(n_scen: int = 64, first: int = 0, n_obs: int = 128, N: int = 40) -> 
     return _assemble(model, scens, f"quad-3d-S{n_scen}-M{n_obs}-N{N}")
 
 
+def closed_loop(n_scen: int = 256, first: int = 0, N: int = 16, duration: float = 25.0):
+    """Receding-horizon quadrotor runs shaped like the paper's simulation
+    (Sec. V-B): a 70 x 20 x 6 m volume (flight along +y from (0, 0, 1) to
+    (0, 70, 1)), 32 polyhedra of 6-20 faces (8 in a sparse first half, 24 in
+    a dense second half), horizon N = 16, dt = 0.1 s, and a reference of
+    `duration` seconds interpolated through the start, 5 random waypoints and
+    the goal.  Returns (scene, ref): the scene holds the first horizon window
+    (s_ref, s_init = s_ref, u_init = 0); ref[s] is scenario s's reference for
+    every control step, [round(duration / dt) + N + 1][ns] (the goal, at rest,
+    after the end)."""
+    model = quad_model()
+    T = int(round(duration / model.dt))
+    scens, refs = [], []
+    for s in range(first, first + n_scen):
+        rng = np.random.default_rng([6, s])
+        start = np.array([0.0, 0.0, 1.0])
+        goal = np.array([0.0, 70.0, 1.0])
+        wy = np.sort(rng.uniform(5.0, 65.0, 5))
+        pts = np.vstack([start, np.stack([rng.uniform(-5, 5, 5), wy, rng.uniform(1.0, 3.0, 5)], 1), goal])
+        seg = np.linalg.norm(np.diff(pts, axis=0), axis=1)
+        tk = np.concatenate([[0.0], np.cumsum(seg)]) / seg.sum() * duration
+        tt = np.arange(T + N + 1) * model.dt
+        ref = np.zeros((T + N + 1, model.ns))
+        for i in range(3):
+            ref[:, i] = np.interp(tt, tk, pts[:, i])
+        ref[:-1, 3:6] = np.diff(ref[:, 0:3], axis=0) / model.dt
+        ref[tt >= duration, 3:6] = 0.0
+        obs = []
+        while len(obs) < 32:
+            dense = len(obs) >= 8
+            ctr = np.array([rng.uniform(-10, 10), rng.uniform(35, 68) if dense else rng.uniform(3, 35), rng.uniform(0, 6)])
+            if min(np.linalg.norm(ctr - start), np.linalg.norm(ctr - goal)) < 2.5:
+                continue
+            C, off = random_polyhedron(rng, int(rng.integers(6, 21)), 0.3, 1.5)
+            obs.append((C, off, ctr))
+        scens.append(_Scen(obs, _quad_parts(), N, ref[:N + 1].copy(), np.zeros((N, model.nu))))
+        refs.append(ref)
+    return _assemble(model, scens, f"closed-loop-quad-S{n_scen}-N{N}"), np.stack(refs)
+
+
 def subset(scene: Scene, idx) -> Scene:
     """The scenarios ``idx`` of ``scene`` as a scene of their own."""
     idx = list(idx)
