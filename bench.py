@@ -112,6 +112,27 @@ def pair_bytes(scene, itemsize=4):
     return out
 
 
+def shard_first(rank: int, per_rank: int) -> int:
+    """Weak scaling: rank r solves its own scenarios r*S .. (r+1)*S - 1 (their
+    seeds), so no data crosses ranks."""
+    return rank * per_rank
+
+
+def reduce_over_ranks(tot, dist, device):
+    """Whole-job totals of the per-rank vector `tot` (solves, converged
+    scenarios, timed ms, algorithmic bytes, kernel ms, launches, pair units):
+    sums over ranks, except the timed region (index 2), which is the slowest
+    rank's."""
+    import torch
+    t = torch.tensor(np.asarray(tot, dtype=np.float64), device=device)
+    tmax = t.clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    out = t.cpu().numpy()
+    out[2] = float(tmax[2].item())
+    return out
+
+
 def gpu_arm(args):
     import torch
 
@@ -129,7 +150,7 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
 
     S = args.scen
-    scene = synth.config3(n_scen=S, first=rank * S)
+    scene = synth.config3(n_scen=S, first=shard_first(rank, S))
     ctx = binding.Context(local)
     ds = binding.DeviceScene(ctx, scene, torch.float32)
     pb = binding.Problem(ds)
@@ -223,12 +244,8 @@ def gpu_arm(args):
     tot = np.array([qp_solves, converged, ms, algo_bytes, prof["pair_ms"], prof["traj_ms"], prof["pair_launches"],
                     pair_units], dtype=np.float64)
     if dist:
-        t = torch.tensor(tot, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tot = t.cpu().numpy()
-        ms = float(tmax[2].item())
+        tot = reduce_over_ranks(tot, dist, dev)
+        ms = float(tot[2])
     value = tot[0] / (ms / 1e3)
     admm_rate = tot[1] / (ms / 1e3)
 
@@ -324,12 +341,59 @@ def gpu_arm(args):
     }
     if clk:
         out["clocks"] = clk
+    if rank == 0 and args.closed_loop > 0:
+        out["closed_loop"] = closed_loop(ctx, args, params, world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene, params, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def closed_loop(ctx, args, params, with_oracle):
+    """Receding-horizon runs shaped like the paper's simulation (Sec. V-B):
+    quadrotor, 32 polyhedra, N = 16, 25 s reference, 20 x 20 x 6 m sensing;
+    every scenario advanced by args.closed_loop control steps in one
+    oca_mpc_run call.  The oracle's loop is timed beside it on 2 scenarios."""
+    from paper_2406_07048_gb300 import binding, synth
+    S, C, mi = 256, args.closed_loop, 50
+    sc, ref = synth.closed_loop(S)
+    x0 = ref[:, 0].copy()
+    ds = binding.DeviceScene(ctx, sc, torch.float32)
+    kw = dict(params)
+    kw["max_iter"] = mi
+    kw.pop("flags", None)
+    binding.mpc_run(ds, ref, sc.obs_center, x0, 2, **kw)  # warm the path
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = binding.mpc_run(ds, ref, sc.obs_center, x0, C, **kw)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    xh = g["x_hist"].double().cpu().numpy()
+    uh = g["u_hist"].double().cpu().numpy()
+    col = g["collided"].cpu().numpy()
+    m = sc.model
+    e = xh[:, :C + 1] - ref[:, :C + 1]
+    cost = (e * e * m.Qs).sum(axis=(1, 2)) + (uh * uh * m.Qu).sum(axis=(1, 2))
+    out = {"workload": f"closed loop, 3-D quadrotor, {S} scenarios x {C} control steps (dt 0.1 s), 32 polyhedra in "
+                       f"70x20x6 m, N=16, sensing 20x20x6 m, warm-started ADMM max_iter {mi}, FP32",
+           "control_steps_per_s": S * C / dt, "wall_s": dt,
+           "mean_admm_iterations_per_step": float(g["iters"].float().mean()),
+           "success_rate": float(np.mean(col < 0)), "navigation_cost_mean": float(cost.mean())}
+    if with_oracle:
+        import oracle
+        sub = synth.subset(sc, [0, 1])
+        cs = min(C, 10)
+        t0 = time.perf_counter()
+        oracle.mpc_run(sub, ref[:2], x0[:2], cs, max_iter=mi, **{k: kw[k] for k in
+                                                                  ("sigma", "eps_pri", "eps_dual", "prox", "rho_box",
+                                                                   "damp")})
+        od = time.perf_counter() - t0
+        out["oracle"] = {"control_steps_per_s": 2 * cs / od, "sample": f"2 scenarios x {cs} control steps",
+                         "cores": oracle.num_threads()}
+    ds.close()
+    return out
 
 
 def _kernel_sha():
@@ -423,6 +487,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warps", type=int, default=0, help="warps per tile (0: autotune)")
     ap.add_argument("--riccati-f32", action="store_true", help="factorise the trajectory QP in FP32")
+    ap.add_argument("--closed-loop", type=int, default=250, help="control steps of the closed-loop line (0: off)")
     ap.add_argument("--prox", type=float, default=None, help="proximal weight of the pair QP (default: library default)")
     ap.add_argument("--damp", type=float, default=None, help="proximal damping of the trajectory step")
     args = ap.parse_args()
