@@ -341,6 +341,8 @@ def gpu_arm(args):
     }
     if clk:
         out["clocks"] = clk
+    if rank == 0 and not args.no_lemke:
+        out["pair_solver_comparison"] = solver_comparison(ds, s0, y0, params)
     if rank == 0 and args.closed_loop > 0:
         out["closed_loop"] = closed_loop(ctx, args, params, world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -351,11 +353,43 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def solver_comparison(ds, s0, y_cold, params):
+    """Step 1 of one ADMM iteration on the benchmark's scenes (cold start) by
+    the hot path's solver and by the paper's Lemke route (one thread per LCP
+    row), each timed with CUDA events over 3 launches after a warm-up."""
+    import torch
+
+    from paper_2406_07048_gb300 import binding
+    zeta = torch.zeros(ds.n_pairs, dtype=ds.dtype, device=ds.device)
+    xi = torch.zeros(ds.scene.dim, ds.n_pairs, dtype=ds.dtype, device=ds.device)
+    prox = params["prox"]
+    res = {}
+    for name, fn in (("semismooth_newton", lambda: binding.pair_qp(ds, s0, zeta, xi, y_cold, prox=prox, want_v=True)),
+                     ("lemke", lambda: binding.pair_qp_lemke(ds, s0, zeta, xi, y_cold, prox=prox))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        st = out["status"].cpu().numpy()
+        res[name] = {"ms_per_launch": ms, "pair_qp_solves_per_s": ds.n_pairs / (ms / 1e3),
+                     "ok_fraction": float((st == 0).mean())}
+    res["workload"] = f"step 1 of the first ADMM iteration, {ds.n_pairs} pairs, prox {prox}, FP32 (launch includes poses)"
+    res["speedup"] = res["lemke"]["ms_per_launch"] / res["semismooth_newton"]["ms_per_launch"]
+    return res
+
+
 def closed_loop(ctx, args, params, with_oracle):
     """Receding-horizon runs shaped like the paper's simulation (Sec. V-B):
     quadrotor, 32 polyhedra, N = 16, 25 s reference, 20 x 20 x 6 m sensing;
     every scenario advanced by args.closed_loop control steps in one
     oca_mpc_run call.  The oracle's loop is timed beside it on 2 scenarios."""
+    import torch
+
     from paper_2406_07048_gb300 import binding, synth
     S, C, mi = 256, args.closed_loop, 50
     sc, ref = synth.closed_loop(S)
@@ -487,6 +521,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warps", type=int, default=0, help="warps per tile (0: autotune)")
     ap.add_argument("--riccati-f32", action="store_true", help="factorise the trajectory QP in FP32")
+    ap.add_argument("--no-lemke", action="store_true", help="skip the pair-solver comparison line")
     ap.add_argument("--closed-loop", type=int, default=250, help="control steps of the closed-loop line (0: off)")
     ap.add_argument("--prox", type=float, default=None, help="proximal weight of the pair QP (default: library default)")
     ap.add_argument("--damp", type=float, default=None, help="proximal damping of the trajectory step")

@@ -224,6 +224,20 @@ oca_status oca_pair_qp_batch(oca_ctx *ctx, const oca_scene *scene, const oca_mod
                              const void *y_in, void *y_out, void *v_out, void *obj_out,
                              int32_t *status_out, void *stream);
 
+/* The same pair QPs as oca_pair_qp_batch by the paper's own route
+ * (Sec. IV-C): y_e of the robot face with the largest b eliminated through
+ * b^T lambda = 1 (eqn:const_least_square_ineq), the KKT conditions
+ * (eqn:kkt_conditions) as the LCP w = M z + q (eqn:linear_complementarity_problem),
+ * solved by Lemke's complementary pivoting with one GPU thread per LCP row
+ * (one warp per pair).  A comparison kernel for the semismooth Newton /
+ * active-set solvers of oca_pair_qp_batch (same arguments and outputs;
+ * y_out must not alias y_in).  Requires fr_max + fo_max + 1 <= 32
+ * (else OCA_ERR_UNSUPPORTED).  status_out: OCA_PAIR_OK, OCA_PAIR_ITER_CAP
+ * (pivot cap), OCA_PAIR_DEGENERATE (ray termination). */
+oca_status oca_pair_qp_lemke_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                                   const void *states, const void *zeta, const void *xi, double prox,
+                                   const void *y_in, void *y_out, void *v_out, void *obj_out,
+                                   int32_t *status_out, void *stream);
 /* Whole ADMM solves of every scenario (Sec. IV-B), Gauss-Seidel order:
  * step 1 pair QPs, step 2 one LQ (SQP) step of the trajectory problem with
  * linearised dynamics and Gauss-Newton-linearised pair residuals, solved by

@@ -75,7 +75,7 @@ EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create"
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
             "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
             "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward",
-            "oca_mpc_run"]
+            "oca_mpc_run", "oca_pair_qp_lemke_batch"]
 
 
 def lib():
@@ -126,6 +126,8 @@ def lib():
         L.oca_mpc_run.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), C.POINTER(MpcParams), P, I, P, P,
                                   P, P, P, P, P, P, P, P, P, P, P]
         L.oca_mpc_run.restype = I
+        L.oca_pair_qp_lemke_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, D, P, P, P, P, P, P]
+        L.oca_pair_qp_lemke_batch.restype = I
         _lib = L
     return _lib
 
@@ -304,6 +306,19 @@ def pair_qp(ds: DeviceScene, states, zeta, xi, y_in, prox: float = 0.0, y_out=No
     _check(lib().oca_pair_qp_batch(ds.ctx.h, ds.h, C.byref(ds.model), _ptr(states), _ptr(zeta), _ptr(xi),
                                    float(prox), _ptr(y_in), _ptr(y_out), _ptr(v), _ptr(obj), _ptr(status),
                                    _stream(stream)), "oca_pair_qp_batch")
+    return dict(y=y_out, v=v, obj=obj, status=status)
+
+
+def pair_qp_lemke(ds: DeviceScene, states, zeta, xi, y_in, prox: float = 0.0, stream=None):
+    """oca_pair_qp_lemke_batch (the paper's Lemke route): y_out, v, obj, status."""
+    P = ds.n_pairs
+    y_out = torch.zeros_like(y_in)
+    v = torch.empty(ds.scene.dim + 1, P, dtype=ds.dtype, device=ds.device)
+    obj = torch.empty(P, dtype=ds.dtype, device=ds.device)
+    status = torch.empty(P, dtype=torch.int32, device=ds.device)
+    _check(lib().oca_pair_qp_lemke_batch(ds.ctx.h, ds.h, C.byref(ds.model), _ptr(states), _ptr(zeta), _ptr(xi),
+                                         float(prox), _ptr(y_in), _ptr(y_out), _ptr(v), _ptr(obj), _ptr(status),
+                                         _stream(stream)), "oca_pair_qp_lemke_batch")
     return dict(y=y_out, v=v, obj=obj, status=status)
 
 

@@ -354,10 +354,45 @@ __global__ void k_cast_d2t(const double *x, long long n, T *y) {
     if (i < n) y[i] = T(x[i]);
 }
 
+
+template <typename T>
+oca_status lemke_impl(oca_scene *sc, const oca_model *m, const void *states, const void *zeta, const void *xi,
+                      double prox, const void *y_in, void *y_out, void *v_out, void *obj_out, int32_t *status_out,
+                      cudaStream_t st) {
+    PoseArgs<T> pa;
+    pa.meta = sc->d_meta;
+    pa.n_scen = sc->S;
+    pa.g = make_geom<T>(sc);
+    pa.model = make_model<T>(m);
+    pa.states = static_cast<const T *>(states);
+    pa.pose = static_cast<T *>(sc->d_pose);
+    pa.Qtot = sc->Qtot;
+    pa.scen_status = nullptr;
+    OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
+    LemkeArgs<T> a;
+    a.meta = sc->d_meta;
+    a.g = make_geom<T>(sc);
+    a.pose = static_cast<const T *>(sc->d_pose);
+    a.Qtot = sc->Qtot;
+    a.P = sc->P;
+    a.n_scen = sc->S;
+    a.zeta = static_cast<const T *>(zeta);
+    a.xi = static_cast<const T *>(xi);
+    a.y_in = static_cast<const T *>(y_in);
+    a.y_out = static_cast<T *>(y_out);
+    a.v_out = static_cast<T *>(v_out);
+    a.obj_out = static_cast<T *>(obj_out);
+    a.status_out = status_out;
+    a.prox = T(prox);
+    OCA_CK(launch_lemke<T>(a, sc->dim, st));
+    return OCA_OK;
+}
+
 template <typename T>
 oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *s,
                      void *u, void *y, void *zeta, void *xi, const oca_admm_report *rep, cudaStream_t st,
-                     void *tape = nullptr, const unsigned char *obs_mask = nullptr) {
+                     void *tape = nullptr, const unsigned char *obs_mask = nullptr,
+                     cudaGraphExec_t *graph_cache = nullptr) {
     k_reset<<<(sc->S + 255) / 256, 256, 0, st>>>(sc->d_status, sc->S, sc->d_iter, sc->d_active);
     OCA_CK(cudaGetLastError());
     const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
@@ -503,8 +538,10 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     };
     const int G = 8;  // iterations per chunk between host checks
     const long long n_launch = (long long)pr->max_iter + 1;  // j = 0..max_iter
-    cudaGraphExec_t exec = nullptr;
-    if (st != nullptr && n_launch > G && !tp) {
+    // graph_cache: a caller that solves repeatedly with the same arguments
+    // (the closed loop) keeps the instantiated graph between calls
+    cudaGraphExec_t exec = graph_cache ? *graph_cache : nullptr;
+    if (!exec && st != nullptr && n_launch > G && !tp) {
         cudaGraph_t graph = nullptr;
         OCA_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         capturing = true;
@@ -519,6 +556,7 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
         cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) return OCA_ERR_CUDA;
+        if (graph_cache) *graph_cache = exec;
     }
     oca_status out = OCA_OK;
     *sc->h_active = sc->S;
@@ -553,7 +591,7 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
         }
         if (*sc->h_active <= 0) break;
     }
-    if (exec) cudaGraphExecDestroy(exec);
+    if (exec && !graph_cache) cudaGraphExecDestroy(exec);
     if (out != OCA_OK) return out;
     dim3 gg(64, sc->S);
     k_gather<T><<<gg, 256, 0, st>>>(sc->d_meta, rep->iters, static_cast<const T *>(sc->d_y2), static_cast<T *>(y), sc->P,
@@ -726,16 +764,22 @@ oca_status mpc_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr
     int max_blk = 1;
     for (const ScenMeta &m2 : sc->meta) max_blk = std::max(max_blk, m2.M * m2.NP);
     OCA_CK(cudaMemsetAsync(collided, 0xff, sizeof(int32_t) * sc->S, st));
-    for (int c = 0; c < mp->n_steps; ++c) {
+    cudaGraphExec_t graph = nullptr;  // the iteration graph, the same for every control step
+    oca_status out = OCA_OK;
+    for (int c = 0; c < mp->n_steps && out == OCA_OK; ++c) {
         a.c = c;
-        OCA_CK(launch_mpc<T>(a, 0, sc->S, max_blk, st));
-        if (c > 0) OCA_CK(launch_mpc<T>(a, 1, sc->S, max_blk, st));
-        const oca_status e = admm_impl<T>(sc, m, pr, s_ref, s, u, y, zeta, xi, &rep, st, nullptr, sc->d_mask);
-        if (e != OCA_OK) return e;
-        OCA_CK(launch_mpc<T>(a, 2, sc->S, max_blk, st));
-        OCA_CK(launch_mpc<T>(a, 3, sc->S, max_blk, st));
+        if (launch_mpc<T>(a, 0, sc->S, max_blk, st) != cudaSuccess ||
+            (c > 0 && launch_mpc<T>(a, 1, sc->S, max_blk, st) != cudaSuccess)) {
+            out = OCA_ERR_CUDA;
+            break;
+        }
+        out = admm_impl<T>(sc, m, pr, s_ref, s, u, y, zeta, xi, &rep, st, nullptr, sc->d_mask, &graph);
+        if (out == OCA_OK && (launch_mpc<T>(a, 2, sc->S, max_blk, st) != cudaSuccess ||
+                              launch_mpc<T>(a, 3, sc->S, max_blk, st) != cudaSuccess))
+            out = OCA_ERR_CUDA;
     }
-    return OCA_OK;
+    if (graph) cudaGraphExecDestroy(graph);
+    return out;
 }
 
 void free_scene(oca_scene *sc) {
@@ -1164,6 +1208,23 @@ oca_status oca_mpc_run(oca_ctx *ctx, const oca_scene *scene, const oca_model *mo
                                u_hist, iters_hist, collided, st);
     return mpc_impl<double>(sc, model, params, mpc, ref, T_ref, obs_center, x, s_ref, s, u, y, zeta, xi, x_hist,
                             u_hist, iters_hist, collided, st);
+}
+
+
+oca_status oca_pair_qp_lemke_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model, const void *states,
+                                   const void *zeta, const void *xi, double prox, const void *y_in, void *y_out,
+                                   void *v_out, void *obj_out, int32_t *status_out, void *stream) {
+    if (!ctx || !scene || !states || !zeta || !xi || !y_in || !y_out || !(prox >= 0.0) || !std::isfinite(prox))
+        return OCA_ERR_INVALID_ARGUMENT;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    const oca_status e = check_model(sc, model);
+    if (e != OCA_OK) return e;
+    if (y_out == y_in) return OCA_ERR_INVALID_ARGUMENT;
+    if (sc->FR + sc->FO + 1 > 32) return OCA_ERR_UNSUPPORTED;  // one lane per LCP row
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32)
+        return lemke_impl<float>(sc, model, states, zeta, xi, prox, y_in, y_out, v_out, obj_out, status_out, st);
+    return lemke_impl<double>(sc, model, states, zeta, xi, prox, y_in, y_out, v_out, obj_out, status_out, st);
 }
 
 }  // extern "C"

@@ -273,4 +273,19 @@ struct MpcArgs {
     int c;                 // control step
 };
 
+// the paper's Lemke route for the pair QPs (comparison kernel)
+template <typename T>
+struct LemkeArgs {
+    const ScenMeta *meta;
+    Geom<T> g;
+    const T *pose;       // [PK][Qtot]
+    int Qtot;
+    long long P;
+    int n_scen;
+    const T *zeta, *xi, *y_in;
+    T *y_out, *v_out, *obj_out;
+    int *status_out;
+    T prox;
+};
+
 }  // namespace oca

@@ -33,6 +33,9 @@ cudaError_t launch_adj_alpha(const AdjAlphaArgs<T> &a, int dim, int n_tiles, int
 // closed loop (oca_mpc.cu): stage 0 window/shift/mask, 1 pair shift, 2 plant, 3 collision
 template <typename T>
 cudaError_t launch_mpc(const MpcArgs<T> &a, int stage, int n_scen, int max_blk, cudaStream_t st);
+// the paper's Lemke route for the pair QPs (oca_lemke.cu)
+template <typename T>
+cudaError_t launch_lemke(const LemkeArgs<T> &a, int dim, cudaStream_t st);
 template <typename T>
 cudaError_t launch_adj_finish(const double *gd, const T *obs_C, const int *obs_nf, int M_tot, int FO, int dim,
                               T *grad_d, T *grad_ctr, cudaStream_t st);
