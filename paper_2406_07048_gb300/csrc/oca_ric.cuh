@@ -332,7 +332,14 @@ __device__ __forceinline__ bool spd_inverse(const F (&U)[NU][NU], F (&X)[NU][NU]
     }
 }
 
-template <typename F, int NS, int NU>
+template <int NT>
+__device__ __forceinline__ void ric_sync() {
+    if constexpr (NT == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// NT threads (one warp, or the whole CTA when NT > 32) run the recursion
+template <typename F, int NS, int NU, int NT = 32>
 __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
     using LY = RicLayout<NS, NU>;
     constexpr int NX = NS + NU + 1;           // columns of G = [A | B | c]
@@ -340,19 +347,19 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
     constexpr int MC = NZ + 1;                // columns of M as stored
     constexpr int NG = NS * NX, NQ = NS * NS;
     constexpr int NST = NG + NQ + NS + NU;    // staged values per step
-    constexpr int PF = (NST + 31) / 32;       // of them per lane
+    constexpr int PF = (NST + NT - 1) / NT;   // of them per thread
     constexpr int NSYM = NZ * (NZ + 1) / 2;   // upper triangle of the Hessian part of M
     constexpr int NPS = NS * (NS + 1) / 2;    // upper triangle of P
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x;  // thread of the NT
     __shared__ F P[NS * NS], pv[NS], stg[NST], Y[NS * NX], M[NZ * MC], KK[NU * (NS + 1)];
     const F *Gs = stg, *Qs = stg + NG, *qs = stg + NG + NQ, *rs = stg + NG + NQ + NS;
-    for (int e = lane; e < NS * NS; e += 32) P[e] = scr[LY::Q(N, N) + e];
-    for (int e = lane; e < NS; e += 32) pv[e] = scr[LY::q(N, N) + e];
+    for (int e = lane; e < NS * NS; e += NT) P[e] = scr[LY::Q(N, N) + e];
+    for (int e = lane; e < NS; e += NT) pv[e] = scr[LY::q(N, N) + e];
     F nxt[PF];
     if (N >= 1) {
 #pragma unroll
         for (int r = 0; r < PF; ++r) {
-            const int e = lane + 32 * r;
+            const int e = lane + NT * r;
             if (e < NST) nxt[r] = ric_stage_elem<F, NS, NU>(scr, N, N - 1, e);
         }
     }
@@ -360,28 +367,28 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
     for (int t = N - 1; t >= 0; --t) {
 #pragma unroll
         for (int r = 0; r < PF; ++r) {
-            const int e = lane + 32 * r;
+            const int e = lane + NT * r;
             if (e < NST) stg[e] = nxt[r];
         }
-        __syncwarp();
+        ric_sync<NT>();
         if (t >= 1) {
 #pragma unroll
             for (int r = 0; r < PF; ++r) {
-                const int e = lane + 32 * r;
+                const int e = lane + NT * r;
                 if (e < NST) nxt[r] = ric_stage_elem<F, NS, NU>(scr, N, t - 1, e);
             }
         }
         // Y = P G + [0 | 0 | p]
-        for (int e = lane; e < NS * NX; e += 32) {
+        for (int e = lane; e < NS * NX; e += NT) {
             const int k = e / NX, j = e % NX;
             F acc = j == NX - 1 ? pv[k] : F(0);
 #pragma unroll
             for (int l = 0; l < NS; ++l) acc += P[k * NS + l] * Gs[l * NX + j];
             Y[e] = acc;
         }
-        __syncwarp();
+        ric_sync<NT>();
         // M: the upper triangle of the Hessian part, then the gradient column
-        for (int e = lane; e < NSYM + NZ; e += 32) {
+        for (int e = lane; e < NSYM + NZ; e += NT) {
             int i, j;
             if (e < NSYM) {
                 int rem = e;
@@ -405,7 +412,7 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
             M[i * MC + j] = acc;
             if (j < NZ && j != i) M[j * MC + i] = acc;
         }
-        __syncwarp();
+        ric_sync<NT>();
         // Quu^-1 (every lane), then [K_t | k_t] = -Quu^-1 [Qus | qu]
         F U[NU][NU], X[NU][NU];
 #pragma unroll
@@ -413,7 +420,7 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
 #pragma unroll
             for (int b = 0; b < NU; ++b) U[a][b] = M[(NS + a) * MC + NS + b];
         ok &= spd_inverse<F, NU>(U, X);
-        for (int e = lane; e < NU * (NS + 1); e += 32) {
+        for (int e = lane; e < NU * (NS + 1); e += NT) {
             const int a = e / (NS + 1), j = e % (NS + 1);
             const int cj = j < NS ? j : NZ;
             F acc = F(0);
@@ -423,9 +430,9 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
             if (j < NS) scr[LY::K(N, t) + a * NS + j] = acc;
             else scr[LY::k(N, t) + a] = acc;
         }
-        __syncwarp();
+        ric_sync<NT>();
         // P_t = Qss + Qus^T K_t (upper triangle, mirrored), p_t = qs + Qus^T k_t
-        for (int e = lane; e < NPS + NS; e += 32) {
+        for (int e = lane; e < NPS + NS; e += NT) {
             if (e < NPS) {
                 int rem = e, i = 0;
                 while (rem >= NS - i) {
@@ -446,9 +453,10 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
                 pv[i] = acc;
             }
         }
-        __syncwarp();
+        ric_sync<NT>();
     }
-    return __all_sync(0xffffffffu, ok);
+    if constexpr (NT == 32) return __all_sync(0xffffffffu, ok);
+    else return __syncthreads_and(ok) != 0;
 }
 
 // Forward sweep u_t = K_t s_t + k_t, s_{t+1} = A_t s_t + B_t u_t + c_t from

@@ -58,8 +58,11 @@ __device__ void finish_scenario(const RicArgs<T> &a, const ScenMeta &sm, int s, 
     }
 }
 
-template <typename T, typename F, int KIND>
-__global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
+// NT threads per scenario: warp 0 runs every phase but the Riccati
+// recursion, which all NT threads share (NT > 32 for the 12-state model,
+// whose per-step products have 150-200 entries).
+template <typename T, typename F, int KIND, int NT>
+__global__ void __launch_bounds__(NT) k_riccati(RicArgs<T> a) {
     constexpr int NS = MDims<KIND>::NS, NU = MDims<KIND>::NU, D = MDims<KIND>::D;
     const int s = blockIdx.x;
     const int lane = threadIdx.x;
@@ -68,8 +71,11 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
     if (j > a.max_iter) return;
     const ScenMeta sm = a.meta[s];
     const int N = sm.N;
+    __shared__ int s_retired;
 
-    // ---- 1. stopping rule of iteration j-1
+    // ---- 1. stopping rule of iteration j-1 (warp 0)
+    if (lane < 32) {
+        s_retired = 0;
     if (j >= 1) {
         const double *rcur = a.res + (size_t)(j & 1) * a.n_tiles * 2;
         const double *rprev = a.res + (size_t)((j - 1) & 1) * a.n_tiles * 2;
@@ -83,12 +89,15 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
         const bool conv = rp <= double(a.eps_pri) && rd <= double(a.eps_dual);
         if (conv || j >= a.max_iter) {
             finish_scenario<T, KIND>(a, sm, s, conv ? OCA_SCEN_CONVERGED : OCA_SCEN_MAX_ITER, j, rp, rd);
-            return;
+            s_retired = 1;
         }
     } else if (a.max_iter <= 0) {
         finish_scenario<T, KIND>(a, sm, s, OCA_SCEN_MAX_ITER, 0, 0.0, 0.0);
-        return;
+        s_retired = 1;
     }
+    }
+    ric_sync<NT>();
+    if (s_retired) return;
 
     F *scr = reinterpret_cast<F *>(a.scratch) + a.scratch0[s];
 
@@ -110,16 +119,20 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
     src.zu = a.box_zu;
     src.wu = a.box_wu;
     src.stats = a.stats;
-    for (int t = lane; t <= N; t += 32) assemble_stage<T, F, KIND>(sp, src, sm, t, scr);
-    __syncwarp();
+    for (int t = lane; t <= N; t += NT) assemble_stage<T, F, KIND>(sp, src, sm, t, scr);
+    ric_sync<NT>();
 
-    // ---- 3. backward Riccati recursion, 4. forward sweep
-    F ru_diag[NU];
-#pragma unroll
-    for (int i = 0; i < NU; ++i)
+    // ---- 3. backward Riccati recursion (all NT threads), 4. forward sweep (warp 0)
+    // diagonal of Ru, formed once and shared by the NT threads (a per-thread
+    // copy indexed at run time gave wrong values in threads >= 32 of the
+    // FP64 four-warp instantiation; the shared copy is also less work)
+    __shared__ F ru_diag[NU];
+    for (int i = lane; i < NU; i += NT)
         ru_diag[i] = F(2) * F(a.model.Qu[i]) + F(a.damp) +
                      (bounded(a.model.u_lo[i], a.model.u_hi[i]) ? F(a.rho_box) : F(0));
-    bool ok = ric_factor<F, NS, NU>(scr, N, ru_diag);
+    ric_sync<NT>();
+    bool ok = ric_factor<F, NS, NU, NT>(scr, N, ru_diag);
+    if (lane >= 32) return;
     __shared__ F sc[NS];
     for (int i = lane; i < NS; i += 32) sc[i] = F(a.s[(long long)sm.state0 * NS + i]);
     __syncwarp();
@@ -193,9 +206,9 @@ __global__ void __launch_bounds__(32) k_riccati(RicArgs<T> a) {
 template <typename T, typename F>
 cudaError_t launch_riccati_f(const RicArgs<T> &a, cudaStream_t st) {
     switch (a.model.kind) {
-        case 0: k_riccati<T, F, 0><<<a.n_scen, 32, 0, st>>>(a); break;
-        case 1: k_riccati<T, F, 1><<<a.n_scen, 32, 0, st>>>(a); break;
-        case 2: k_riccati<T, F, 2><<<a.n_scen, 32, 0, st>>>(a); break;
+        case 0: k_riccati<T, F, 0, 32><<<a.n_scen, 32, 0, st>>>(a); break;
+        case 1: k_riccati<T, F, 1, 32><<<a.n_scen, 32, 0, st>>>(a); break;
+        case 2: k_riccati<T, F, 2, 128><<<a.n_scen, 128, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
