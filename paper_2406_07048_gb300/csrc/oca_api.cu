@@ -210,15 +210,22 @@ __global__ void k_box_init(const T *x, long long n, int nc, Bounds12<T> b, T *z,
 }
 
 // final y of a scenario retired at iteration j lives in buffer j % 2
+// y of the scenarios whose last iteration left it in the second buffer back
+// into the caller's y: only a pair's own components (lambda_k, k < n_faces
+// of the part; mu_m, m < n_faces of the obstacle; gamma), padding untouched
 template <typename T>
-__global__ void k_gather(const ScenMeta *meta, const int *iters, const T *y2, T *y, long long P, int ny) {
+__global__ void k_gather(const ScenMeta *meta, const int *iters, const int *part_nf, const int *obs_nf, int FR, int FO,
+                         const T *y2, T *y, long long P, int ny) {
     const int s = blockIdx.y;
     if (!(iters[s] & 1)) return;
     const ScenMeta sm = meta[s];
     const long long np = (long long)sm.M * sm.NP * sm.N;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np * ny; k += (long long)gridDim.x * blockDim.x) {
-        const long long c = k / np, p = sm.pair0 + k % np;
-        y[c * P + p] = y2[c * P + p];
+        const long long c = k / np, l = k % np, p = sm.pair0 + l;
+        const int j = (int)(l / ((long long)sm.NP * sm.N)), part = (int)((l / sm.N) % sm.NP);
+        const bool own = c < FR ? c < part_nf[sm.part0 + part]
+                                : (c < FR + FO ? c - FR < obs_nf[sm.obs0 + j] : true);
+        if (own) y[c * P + p] = y2[c * P + p];
     }
 }
 
@@ -594,8 +601,8 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     if (exec && !graph_cache) cudaGraphExecDestroy(exec);
     if (out != OCA_OK) return out;
     dim3 gg(64, sc->S);
-    k_gather<T><<<gg, 256, 0, st>>>(sc->d_meta, rep->iters, static_cast<const T *>(sc->d_y2), static_cast<T *>(y), sc->P,
-                                    sc->ny_max);
+    k_gather<T><<<gg, 256, 0, st>>>(sc->d_meta, rep->iters, sc->d_part_nf, sc->d_obs_nf, sc->FR, sc->FO,
+                                    static_cast<const T *>(sc->d_y2), static_cast<T *>(y), sc->P, sc->ny_max);
     OCA_CK(cudaGetLastError());
     return OCA_OK;
 }

@@ -304,3 +304,40 @@ def test_edge_cases(B, ctx, ora):
         rep = pb.solve(max_iter=50)
         rr = ora.admm_batch(sc, max_iter=50)
         assert int(rep["iters"][0]) == rr["iters"][0] or dtype == F32
+
+
+def _padding_mask(sc):
+    """[P, ny_max] True where a component lies beyond the pair's own face counts."""
+    pad = np.ones((sc.n_pairs, sc.ny_max), dtype=bool)
+    for s in range(sc.n_scen):
+        n = int(sc.horizon[s])
+        for j in range(sc.n_obs(s)):
+            no = int(sc.obs_nf[int(sc.obs_begin[s]) + j])
+            for pt in range(sc.n_parts(s)):
+                nr = int(sc.part_nf[int(sc.part_begin[s]) + pt])
+                p0 = sc.pair_index(s, j, pt, 1)
+                pad[p0:p0 + n, :nr] = False
+                pad[p0:p0 + n, sc.fr_max:sc.fr_max + no] = False
+                pad[p0:p0 + n, sc.fr_max + sc.fo_max] = False
+    return pad
+
+
+@pytest.mark.parametrize("iters", [3, 4])
+def test_admm_y_padding_untouched(B, ctx, iters):
+    """Components of y beyond a pair's face counts are neither read nor
+    written (odd budgets end in the second y buffer and go through the
+    final gather)."""
+    sc = _scene("c3")
+    pad = _padding_mask(sc)
+    assert pad.any()
+    y0 = sc.cold_y()
+    y0[pad] = 7.0
+    ds = B.DeviceScene(ctx, sc, F64)
+    pb = B.Problem(ds, y_init=y0)
+    pb.solve(max_iter=iters, eps_pri=0.0, eps_dual=0.0)
+    y = ds.to_host_pairs(pb.y)
+    assert (y[pad] == 7.0).all()
+    ref = B.Problem(ds)
+    ref.solve(max_iter=iters, eps_pri=0.0, eps_dual=0.0)
+    assert np.array_equal(y[~pad], ds.to_host_pairs(ref.y)[~pad])
+    ds.close()
