@@ -182,6 +182,8 @@ typedef struct {
 } oca_admm_params;
 
 #define OCA_ADMM_RICCATI_F32 1  /* factorise the trajectory QP in FP32 (default FP64) */
+#define OCA_ADMM_FIXED_POINT 2  /* differentiate the fixed point (oca_admm_solve_taped,
+                                   oca_admm_backward): see below                   */
 
 /* Per-scenario results, all device arrays of length S (float arrays: scene dtype). */
 typedef struct {
@@ -274,10 +276,18 @@ oca_status oca_admm_solve(oca_ctx *ctx, const oca_scene *scene, const oca_model 
  * area.  About (max_iter + 1) * (ny_max + dim + 1) * n_pairs elements.
  * Errors: OCA_ERR_INVALID_ARGUMENT. */
 oca_status oca_admm_tape_bytes(const oca_scene *scene, const oca_model *model, int32_t max_iter, int64_t *bytes);
+/* Size in bytes of the one-iterate tape of the fixed-point form
+ * (OCA_ADMM_FIXED_POINT): the final iterate and the same work area, about
+ * (2 ny_max + 2 dim + 2) * n_pairs elements, independent of max_iter.
+ * Errors: OCA_ERR_INVALID_ARGUMENT. */
+oca_status oca_admm_fixed_point_tape_bytes(const oca_scene *scene, const oca_model *model, int64_t *bytes);
 /* oca_admm_solve that also records its iterates in `tape` (caller-owned
  * device memory, 256-byte aligned, tape_bytes >= oca_admm_tape_bytes(...,
  * params->max_iter); else OCA_ERR_INVALID_ARGUMENT / OCA_ERR_CAPACITY).
- * Same results as oca_admm_solve; runs without iteration graphs. */
+ * Same results as oca_admm_solve; runs without iteration graphs.
+ * With OCA_ADMM_FIXED_POINT in params->flags it records only the returned
+ * iterate (tape_bytes >= oca_admm_fixed_point_tape_bytes) and runs as
+ * oca_admm_solve does, iteration graphs included. */
 oca_status oca_admm_solve_taped(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
                                 const oca_admm_params *params, const void *s_ref, void *s, void *u, void *y,
                                 void *zeta, void *xi, const oca_admm_report *report, void *tape, int64_t tape_bytes,
@@ -299,7 +309,17 @@ oca_status oca_admm_solve_taped(oca_ctx *ctx, const oca_scene *scene, const oca_
  *                                    obstacle (offsets d_m + c_m . delta);
  *   grad_state0     [S][ns]          dL/ds_0.
  * prox must be > 0 (else OCA_ERR_UNSUPPORTED).  Scenarios whose solve
- * FAILED, or that ran no iteration, get meaningless gradients. */
+ * FAILED, or that ran no iteration, get meaningless gradients.
+ *
+ * Fixed-point form (OCA_ADMM_FIXED_POINT in params->flags, the tape of a
+ * fixed-point taped solve): the derivative of the solve's limit xs = T(xs)
+ * instead of the executed iterations, by the implicit function theorem,
+ * d xs / d theta = (I - dT/dx)^-1 dT/dtheta, its transpose applied as the
+ * Neumann series sum_i (dT/dx^T)^i: params->max_iter reverse steps of the
+ * same adjoint iteration, every one at the taped iterate.  Valid for
+ * scenarios that converged; the series converges at the rate the forward
+ * iteration did, so max_iter should be of the order of the iterations the
+ * forward took to converge tightly.  Memory: one iterate, whatever the count. */
 oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
                              const oca_admm_params *params, const void *s_ref, void *tape, int64_t tape_bytes,
                              const int32_t *iters, const void *grad_cost, const void *grad_alpha,

@@ -23,6 +23,7 @@ OCA_OK = 0
 STATUS_NAMES = {0: "OCA_OK", 1: "OCA_ERR_INVALID_ARGUMENT", 2: "OCA_ERR_CUDA", 3: "OCA_ERR_NO_MEMORY",
                 4: "OCA_ERR_UNSUPPORTED", 5: "OCA_ERR_CAPACITY"}
 OCA_ADMM_RICCATI_F32 = 1
+OCA_ADMM_FIXED_POINT = 2
 MAX_OBS_FACES, MAX_PART_FACES, MAX_HORIZON = 24, 8, 256
 
 
@@ -75,7 +76,7 @@ EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create"
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
             "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
             "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward",
-            "oca_mpc_run", "oca_pair_qp_lemke_batch"]
+            "oca_mpc_run", "oca_pair_qp_lemke_batch", "oca_admm_fixed_point_tape_bytes"]
 
 
 def lib():
@@ -117,6 +118,8 @@ def lib():
         L.oca_scale_detect_noalloc.restype = I
         L.oca_admm_tape_bytes.argtypes = [P, C.POINTER(ModelC), I, C.POINTER(C.c_int64)]
         L.oca_admm_tape_bytes.restype = I
+        L.oca_admm_fixed_point_tape_bytes.argtypes = [P, C.POINTER(ModelC), C.POINTER(C.c_int64)]
+        L.oca_admm_fixed_point_tape_bytes.restype = I
         L.oca_admm_solve_taped.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, P, P, P, P,
                                            C.POINTER(Report), P, C.c_int64, P]
         L.oca_admm_solve_taped.restype = I
@@ -349,16 +352,21 @@ def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1
     return rep_t
 
 
-def tape_bytes(ds: DeviceScene, max_iter: int) -> int:
-    """oca_admm_tape_bytes."""
+def tape_bytes(ds: DeviceScene, max_iter: int, fixed_point: bool = False) -> int:
+    """oca_admm_tape_bytes (oca_admm_fixed_point_tape_bytes with fixed_point)."""
     n = C.c_int64(0)
-    _check(lib().oca_admm_tape_bytes(ds.h, C.byref(ds.model), int(max_iter), C.byref(n)), "oca_admm_tape_bytes")
+    if fixed_point:
+        _check(lib().oca_admm_fixed_point_tape_bytes(ds.h, C.byref(ds.model), C.byref(n)),
+               "oca_admm_fixed_point_tape_bytes")
+    else:
+        _check(lib().oca_admm_tape_bytes(ds.h, C.byref(ds.model), int(max_iter), C.byref(n)), "oca_admm_tape_bytes")
     return int(n.value)
 
 
-def new_tape(ds: DeviceScene, max_iter: int) -> torch.Tensor:
-    """A device byte tensor large enough for a taped solve of max_iter iterations."""
-    return torch.empty(tape_bytes(ds, max_iter), dtype=torch.uint8, device=ds.device)
+def new_tape(ds: DeviceScene, max_iter: int, fixed_point: bool = False) -> torch.Tensor:
+    """A device byte tensor large enough for a taped solve of max_iter
+    iterations (one iterate, any count, with fixed_point)."""
+    return torch.empty(tape_bytes(ds, max_iter, fixed_point), dtype=torch.uint8, device=ds.device)
 
 
 def admm_backward(ds: DeviceScene, s_ref, tape, iters, grad_cost, grad_alpha=None, sigma=300.0, prox=1.0,

@@ -45,6 +45,7 @@ struct oca_scene {
     double *d_mpc_f = nullptr;  // per-step report (r_pri, r_dual, cost) [3][S] (scene dtype)
     unsigned char *d_mask = nullptr;  // [M_tot] sensed obstacles
     double *d_box_res = nullptr;  // [S][2]
+    int *d_rev_iters = nullptr;   // fixed-point adjoint: reverse steps per scenario [S]
     int ns_max = 0, nu_max = 0;
     int *h_active = nullptr;
 };
@@ -315,7 +316,9 @@ struct TapeLayout {
     size_t gd_byte, gs0_byte, bytes;
 };
 
-TapeLayout tape_layout(const oca_scene *sc, int kind, int K) {
+// fp (OCA_ADMM_FIXED_POINT): one slot of every iterate region (the final
+// iterate), whatever K is
+TapeLayout tape_layout(const oca_scene *sc, int kind, int K, bool fp = false) {
     const int NS = kind == 0 ? 4 : kind == 1 ? 5 : 12, NU = kind == 2 ? 4 : 2;
     const int D = sc->dim, NSTAT = D * (D + 1) / 2 + D + D * D, PK = D + D * D;
     const long long es = (long long)dsize(sc->dtype);
@@ -328,13 +331,14 @@ TapeLayout tape_layout(const oca_scene *sc, int kind, int K) {
     L.s_slot = up(sc->n_states * NS);
     L.u_slot = up(sc->n_ctrls * NU);
     L.box_slot = up(2 * sc->n_states * NS + 2 * sc->n_ctrls * NU);
+    const long long n1 = fp ? 1 : (long long)K + 1, n0 = fp ? 1 : (long long)K;  // slots
     long long o = 0;
-    L.y = o;   o += (long long)(K + 1) * L.y_slot;
-    L.zx = o;  o += (long long)K * L.zx_slot;
-    L.st = o;  o += (long long)K * L.st_slot;
-    L.s = o;   o += (long long)(K + 1) * L.s_slot;
-    L.u = o;   o += (long long)(K + 1) * L.u_slot;
-    L.box = o; o += (long long)(K + 1) * L.box_slot;
+    L.y = o;   o += n1 * L.y_slot;
+    L.zx = o;  o += n0 * L.zx_slot;
+    L.st = o;  o += n0 * L.st_slot;
+    L.s = o;   o += n1 * L.s_slot;
+    L.u = o;   o += n1 * L.u_slot;
+    L.box = o; o += n1 * L.box_slot;
     L.yb = o;  o += 2 * L.y_slot;
     L.zb = o;  o += L.zx_slot;
     L.sb = o;  o += L.s_slot;
@@ -432,9 +436,12 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     pa.scen_status = nullptr;
     OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
 
-    // tape (oca_admm_solve_taped): iterate 0 now, iterate j+1 after launch j
+    // tape (oca_admm_solve_taped): iterate 0 now, iterate j+1 after launch j;
+    // a fixed-point tape (OCA_ADMM_FIXED_POINT) takes the final iterate only,
+    // after the solve, which then runs as an untaped one
     TapeLayout TL{};
-    T *tp = static_cast<T *>(tape);
+    const bool fp_tape = tape && (pr->flags & OCA_ADMM_FIXED_POINT);
+    T *tp = fp_tape ? nullptr : static_cast<T *>(tape);
     const size_t es = sizeof(T);
     const size_t box_s = (size_t)sc->n_states * NS, box_u = (size_t)sc->n_ctrls * NU;
     auto tape_box = [&](int slot) -> cudaError_t {
@@ -604,9 +611,33 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     k_gather<T><<<gg, 256, 0, st>>>(sc->d_meta, rep->iters, sc->d_part_nf, sc->d_obs_nf, sc->FR, sc->FO,
                                     static_cast<const T *>(sc->d_y2), static_cast<T *>(y), sc->P, sc->ny_max);
     OCA_CK(cudaGetLastError());
+    if (fp_tape) {
+        // the returned iterate of every scenario: y, zeta, xi, s, u as returned;
+        // the statistics and the box block as its last iteration left them
+        // (retired scenarios' entries are not touched after they retire)
+        const TapeLayout FL = tape_layout(sc, m->kind, 0, true);
+        T *ft = static_cast<T *>(tape);
+        const int nstat = sc->dim * (sc->dim + 1) / 2 + sc->dim + sc->dim * sc->dim;
+        OCA_CK(cudaMemcpyAsync(ft + FL.y, y, es * sc->ny_max * (size_t)sc->P, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(ft + FL.zx, zeta, es * (size_t)sc->P, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(ft + FL.zx + sc->P, xi, es * sc->dim * (size_t)sc->P, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(ft + FL.st, sc->d_stats, es * nstat * (size_t)sc->Qtot, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(ft + FL.s, s, es * box_s, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(ft + FL.u, u, es * box_u, cudaMemcpyDeviceToDevice, st));
+        T *dst = ft + FL.box;
+        OCA_CK(cudaMemcpyAsync(dst, zs, es * box_s, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(dst + box_s, ws, es * box_s, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(dst + 2 * box_s, zu, es * box_u, cudaMemcpyDeviceToDevice, st));
+        OCA_CK(cudaMemcpyAsync(dst + 2 * box_s + box_u, wu, es * box_u, cudaMemcpyDeviceToDevice, st));
+    }
     return OCA_OK;
 }
 
+
+__global__ void k_rev_iters(const int32_t *iters, int K, int S, int *out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) out[s] = iters[s] > 0 ? K : 0;
+}
 
 template <typename T>
 oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *tape,
@@ -614,7 +645,15 @@ oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_param
                          void *grad_ctr, void *grad_s0, cudaStream_t st) {
     const int K = pr->max_iter;
     const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
-    const TapeLayout TL = tape_layout(sc, m->kind, K);
+    // fixed point: K reverse steps of the iteration map, all at the one taped
+    // iterate (zero slot strides), for every scenario that ran an iteration
+    const bool fp = (pr->flags & OCA_ADMM_FIXED_POINT) != 0;
+    const TapeLayout TL = tape_layout(sc, m->kind, K, fp);
+    if (fp) {
+        k_rev_iters<<<(sc->S + 255) / 256, 256, 0, st>>>(iters, K, sc->S, sc->d_rev_iters);
+        OCA_CK(cudaGetLastError());
+        iters = sc->d_rev_iters;
+    }
     T *tp = static_cast<T *>(tape);
     unsigned char *tb = static_cast<unsigned char *>(tape);
     // zero the work area and the accumulators
@@ -629,12 +668,12 @@ oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_param
     tv.s = tp + TL.s;
     tv.u = tp + TL.u;
     tv.box = tp + TL.box;
-    tv.y_slot = TL.y_slot;
-    tv.zx_slot = TL.zx_slot;
-    tv.stats_slot = TL.st_slot;
-    tv.s_slot = TL.s_slot;
-    tv.u_slot = TL.u_slot;
-    tv.box_slot = TL.box_slot;
+    tv.y_slot = fp ? 0 : TL.y_slot;
+    tv.zx_slot = fp ? 0 : TL.zx_slot;
+    tv.stats_slot = fp ? 0 : TL.st_slot;
+    tv.s_slot = fp ? 0 : TL.s_slot;
+    tv.u_slot = fp ? 0 : TL.u_slot;
+    tv.box_slot = fp ? 0 : TL.box_slot;
     tv.n_states = sc->n_states;
     tv.n_ctrls = sc->n_ctrls;
 
@@ -687,7 +726,7 @@ oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_param
         aa.grad_alpha = static_cast<const T *>(grad_alpha);
         aa.poseb = tp + TL.pb;
         aa.gd = gd;
-        OCA_CK(launch_adj_alpha<T>(aa, sc->dim, sc->n_tiles, W, iters, tp + TL.s, TL.s_slot, NS, sc->S, tp + TL.sf, pa,
+        OCA_CK(launch_adj_alpha<T>(aa, sc->dim, sc->n_tiles, W, iters, tp + TL.s, tv.s_slot, NS, sc->S, tp + TL.sf, pa,
                                    sc->maxQ, st));
     }
 
@@ -709,12 +748,12 @@ oca_status backward_impl(oca_scene *sc, const oca_model *m, const oca_admm_param
     for (int k = K - 1; k >= 0; --k) {
         ta.k = k;
         OCA_CK(launch_adj_traj<T>(ta, sc->S, st));
-        pa.states = tp + TL.s + (long long)k * TL.s_slot;
+        pa.states = tp + TL.s + (long long)k * tv.s_slot;
         OCA_CK(launch_pose<T>(pa, sc->maxQ, st));
         ap.k = k;
-        ap.y_k = tp + TL.y + (long long)k * TL.y_slot;
-        ap.y_k1 = tp + TL.y + (long long)(k + 1) * TL.y_slot;
-        ap.zx_k = tp + TL.zx + (long long)k * TL.zx_slot;
+        ap.y_k = tp + TL.y + (long long)k * tv.y_slot;
+        ap.y_k1 = tp + TL.y + (long long)(k + 1) * tv.y_slot;
+        ap.zx_k = tp + TL.zx + (long long)k * tv.zx_slot;
         ap.ybar_in = tp + TL.yb + (long long)((k + 1) & 1) * TL.y_slot;
         ap.ybar_out = tp + TL.yb + (long long)(k & 1) * TL.y_slot;
         OCA_CK(launch_adj_pair<T>(ap, sc->dim, sc->n_tiles, W, st));
@@ -805,6 +844,7 @@ void free_scene(oca_scene *sc) {
     cudaFree(sc->d_ric_off);
     cudaFree(sc->d_status);
     cudaFree(sc->d_mpc_i);
+    cudaFree(sc->d_rev_iters);
     cudaFree(sc->d_mpc_f);
     cudaFree(sc->d_mask);
     cudaFree(sc->d_iter);
@@ -1013,6 +1053,7 @@ oca_status oca_scene_create(oca_ctx *ctx, const oca_scene_desc *d, oca_scene **o
         (e = dmalloc(&sc->d_res, sizeof(double) * 4 * (size_t)tiles)) != OCA_OK ||
         (e = dmalloc(&sc->d_status, sizeof(int) * S)) != OCA_OK ||
         (e = dmalloc(&sc->d_mpc_i, sizeof(int) * 2 * S)) != OCA_OK ||
+        (e = dmalloc(&sc->d_rev_iters, sizeof(int) * S)) != OCA_OK ||
         (e = dmalloc(&sc->d_mpc_f, sizeof(double) * 3 * S)) != OCA_OK ||
         (e = dmalloc(&sc->d_mask, (size_t)M_tot)) != OCA_OK ||
         (e = dmalloc(&sc->d_iter, sizeof(int))) != OCA_OK ||
@@ -1142,6 +1183,14 @@ oca_status oca_admm_tape_bytes(const oca_scene *scene, const oca_model *model, i
     return OCA_OK;
 }
 
+oca_status oca_admm_fixed_point_tape_bytes(const oca_scene *scene, const oca_model *model, int64_t *bytes) {
+    if (!scene || !bytes) return OCA_ERR_INVALID_ARGUMENT;
+    oca_status e = check_model(scene, model);
+    if (e != OCA_OK) return e;
+    *bytes = (int64_t)tape_layout(scene, model->kind, 0, true).bytes;
+    return OCA_OK;
+}
+
 static oca_status check_admm_args(const oca_ctx *ctx, const oca_scene *scene, const oca_admm_params *params,
                                   const void *s_ref, const void *s, const void *u, const void *y, const void *zeta,
                                   const void *xi, const oca_admm_report *report) {
@@ -1165,7 +1214,8 @@ oca_status oca_admm_solve_taped(oca_ctx *ctx, const oca_scene *scene, const oca_
     oca_scene *sc = const_cast<oca_scene *>(scene);
     if ((e = check_model(sc, model)) != OCA_OK) return e;
     if (!tape || reinterpret_cast<uintptr_t>(tape) % 256 != 0) return OCA_ERR_INVALID_ARGUMENT;
-    if (tape_bytes < (int64_t)tape_layout(sc, model->kind, params->max_iter).bytes) return OCA_ERR_CAPACITY;
+    const bool fp = (params->flags & OCA_ADMM_FIXED_POINT) != 0;
+    if (tape_bytes < (int64_t)tape_layout(sc, model->kind, params->max_iter, fp).bytes) return OCA_ERR_CAPACITY;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (sc->dtype == OCA_F32) return admm_impl<float>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st, tape);
     return admm_impl<double>(sc, model, params, s_ref, s, u, y, zeta, xi, report, st, tape);
@@ -1183,7 +1233,8 @@ oca_status oca_admm_backward(oca_ctx *ctx, const oca_scene *scene, const oca_mod
     oca_scene *sc = const_cast<oca_scene *>(scene);
     oca_status e = check_model(sc, model);
     if (e != OCA_OK) return e;
-    if (tape_bytes < (int64_t)tape_layout(sc, model->kind, params->max_iter).bytes) return OCA_ERR_CAPACITY;
+    const bool fp = (params->flags & OCA_ADMM_FIXED_POINT) != 0;
+    if (tape_bytes < (int64_t)tape_layout(sc, model->kind, params->max_iter, fp).bytes) return OCA_ERR_CAPACITY;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (sc->dtype == OCA_F32)
         return backward_impl<float>(sc, model, params, s_ref, tape, iters, grad_cost, grad_alpha, grad_obs_offset,

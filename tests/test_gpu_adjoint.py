@@ -214,3 +214,66 @@ def test_alpha_gradient_matches_oracle_fd(B, ctx, ora):
     _check([(fd(_centre(j, i)), g["obs_center"][j, i]) for j in range(sc.obs_d.shape[0]) for i in range(sc.dim)],
            1e-4)
     _check([(fd(_state0(0, i)), g["state0"][0, i]) for i in range(sc.model.ns)], 1e-5)
+
+
+KFP = 8000  # the bicycle scene's ADMM contracts by ~0.998 per iteration: 0.998^8000 ~ 1e-7
+
+
+def _fp_grads(B, ctx, sc, K, dtype, n_rev=None):
+    """Fixed-point form: a solve of K iterations taping its returned iterate,
+    then n_rev (default K) reverse steps at it."""
+    ds = B.DeviceScene(ctx, sc, dtype)
+    pb = B.Problem(ds)
+    tape = B.new_tape(ds, K, fixed_point=True)
+    rep = B.admm_solve(ds, pb.s_ref, pb.s, pb.u, pb.y, pb.zeta, pb.xi, tape=tape, max_iter=K,
+                       flags=B.OCA_ADMM_FIXED_POINT, **KW)
+    gc = torch.ones(sc.n_scen, dtype=dtype, device=ds.device)
+    g = B.admm_backward(ds, pb.s_ref, tape, rep["iters"], gc, max_iter=K if n_rev is None else n_rev,
+                        flags=B.OCA_ADMM_FIXED_POINT, **{k: KW[k] for k in ("sigma", "prox", "rho_box", "damp")})
+    out = {k: v.double().cpu().numpy() for k, v in g.items()}
+    out["cost"] = rep["cost"].double().cpu().numpy()
+    out["tape_bytes"] = tape.numel()
+    return out
+
+
+def test_fixed_point_adjoint_matches_oracle_fd(B, ctx, ora):
+    """The implicit-function gradient of the converged solution (one taped
+    iterate, 8,000 reverse steps) against central differences of the oracle's
+    ADMM run 8,000 iterations from the same start, where the iteration has
+    converged to rounding level and the executed map's derivative equals the
+    fixed point's."""
+    sc = synth.config1()
+    g = _fp_grads(B, ctx, sc, KFP, torch.float64)
+    ref = ora.admm_batch(sc, max_iter=KFP, **KW)
+    assert np.allclose(g["cost"], ref["cost"], rtol=1e-9)
+    rng = np.random.default_rng(11)
+    offs = [(j, m) for j in range(sc.obs_d.shape[0]) for m in range(int(sc.obs_nf[j]))]
+    pick = [offs[i] for i in rng.choice(len(offs), 3, replace=False)]
+    _check([(_fd(ora, sc, KFP, _offset(j, m)), g["obs_offset"][j, m]) for j, m in pick], 1e-4)
+    _check([(_fd(ora, sc, KFP, _centre(j, i)), g["obs_center"][j, i]) for j in (0, 2) for i in range(sc.dim)], 1e-4)
+    _check([(_fd(ora, sc, KFP, _state0(0, i)), g["state0"][0, i]) for i in (0, 2)], 1e-4)
+
+
+def test_fixed_point_adjoint_equals_long_unroll(B, ctx):
+    """At convergence the Neumann series and the unrolled adjoint of the
+    same 8,000 iterations agree; the fixed-point tape holds one iterate
+    (its size does not depend on the iteration count)."""
+    sc = synth.config1()
+    fp = _fp_grads(B, ctx, sc, KFP, torch.float64)
+    un = _gpu_grads(B, ctx, sc, KFP, torch.float64)
+    for k in ("obs_offset", "obs_center", "state0"):
+        scale = np.abs(un[k]).max()
+        assert np.abs(fp[k] - un[k]).max() <= 1e-6 * scale, k
+    ds = B.DeviceScene(ctx, sc, torch.float64)
+    assert B.tape_bytes(ds, 10, fixed_point=True) == B.tape_bytes(ds, KFP, fixed_point=True)
+    assert B.tape_bytes(ds, KFP, fixed_point=True) * 1000 < B.tape_bytes(ds, KFP)
+
+
+def test_fixed_point_series_truncation(B, ctx):
+    """Fewer reverse steps truncate the Neumann series: the gradient moves
+    toward the full one as the step count grows."""
+    sc = synth.config1()
+    full = _fp_grads(B, ctx, sc, KFP, torch.float64)["obs_offset"]
+    errs = [np.abs(_fp_grads(B, ctx, sc, KFP, torch.float64, n_rev=n)["obs_offset"] - full).max()
+            for n in (500, 2000, 5000)]
+    assert errs[0] > errs[1] > errs[2]
