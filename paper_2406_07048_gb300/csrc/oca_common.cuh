@@ -97,6 +97,23 @@ OCA_HD inline T ldg(const T *p) {
 #endif
 }
 
+#ifdef __CUDACC__
+// Asynchronous global -> shared copy of one element (cp.async, 4 or 8 bytes,
+// both addresses aligned to the element size), its group commit and the wait
+// for every group this thread committed.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+#endif
+
 // ---- kernel argument blocks -------------------------------------------------
 template <typename T>
 struct PoseArgs {

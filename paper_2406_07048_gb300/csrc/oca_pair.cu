@@ -91,9 +91,15 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
     const bool valid = q < Q;
     const long long P = a.P;
     const int FR = a.g.FR, FO = a.g.FO;
-    // shared memory: [staged face data 4 x FO x BT] [statistics W x NSTAT x 32] [residuals W x 2 (double)]
+    // shared memory: [staged face data 4 x FO x BT] [next obstacle's pair data W x NPF x 32]
+    // [statistics W x NSTAT x 32] [residuals W x 2 (double)]; the first two with SOLVER 1 only
+    const int NY = FR + FO + 1, NPF = NY + 1 + D;  // y components, zeta, xi
     T *stg = reinterpret_cast<T *>(smem_raw);
-    T *red = stg + (SOLVER == 1 ? 4 * FO * BT : 0);
+    T *pfb = stg + (SOLVER == 1 ? 4 * FO * BT : 0);
+    T *red = pfb + (SOLVER == 1 ? W * NPF * 32 : 0);
+    // this lane's column of its warp's prefetch buffer: component c at pw[c * 32]
+    // (lambda_k at k, mu_m at FR + m, gamma at FR + FO, zeta at NY, xi_i at NY + 1 + i)
+    T *pw = pfb + warp * NPF * 32 + lane;
 
     Lane<T, D> L;
     SsnLane<T, D, NR> SL;
@@ -147,6 +153,25 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
             SL.syb = stg + 2 * FO * BT + tid;
             SL.sq = stg + 3 * FO * BT + tid;
         }
+        // SOLVER 1: the pair data of this warp's next obstacle are copied to
+        // shared memory asynchronously while the current obstacle is solved
+        auto prefetch = [&](int jn) {
+            if constexpr (SOLVER == 1) {
+                if (jn >= sm.M) return;
+                const int gmn = sm.obs0 + jn;
+                if (a.obs_mask && !a.obs_mask[gmn]) return;
+                const long long pn = sm.pair0 + (long long)jn * Q + q;
+                const int non = a.g.obs_nf[gmn];
+                for (int k = 0; k < L.nr; ++k) cp_async_elem(pw + k * 32, y_in + (long long)k * P + pn);
+                for (int m = 0; m < non; ++m) cp_async_elem(pw + (FR + m) * 32, y_in + (long long)(FR + m) * P + pn);
+                cp_async_elem(pw + (FR + FO) * 32, y_in + (long long)(FR + FO) * P + pn);
+                cp_async_elem(pw + NY * 32, a.zeta + pn);
+#pragma unroll
+                for (int i = 0; i < D; ++i) cp_async_elem(pw + (NY + 1 + i) * 32, a.xi + (long long)i * P + pn);
+                cp_async_commit();
+            }
+        };
+        prefetch(warp);
 
         for (int j = warp; j < sm.M; j += W) {
             const int gm = sm.obs0 + j;
@@ -163,12 +188,20 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                     for (int m = 0; m < L.no; ++m) y_out[(long long)(FR + m) * P + p] = y_in[(long long)(FR + m) * P + p];
                     y_out[(long long)(FR + FO) * P + p] = y_in[(long long)(FR + FO) * P + p];
                 }
+                prefetch(j + W);
                 continue;
             }
-            T zeta = a.zeta[p];
-            T xi[D];
+            T zeta, xi[D];
+            if constexpr (SOLVER == 1) {
+                cp_async_wait_all();  // this obstacle's copies (issued by this lane)
+                zeta = pw[NY * 32];
 #pragma unroll
-            for (int i = 0; i < D; ++i) xi[i] = a.xi[(long long)i * P + p];
+                for (int i = 0; i < D; ++i) xi[i] = pw[(NY + 1 + i) * 32];
+            } else {
+                zeta = a.zeta[p];
+#pragma unroll
+                for (int i = 0; i < D; ++i) xi[i] = a.xi[(long long)i * P + p];
+            }
             const T *yb = y_in + p;
             T *yo = y_out + p;
             // ---- one pass over y^j: compressed certificate (A^T lambda, C^T mu,
@@ -192,14 +225,14 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     if (k < L.nr) {
-                        const T yv = yb[(long long)k * P];
+                        const T yv = pw[k * 32];
                         SL.yl[k] = yv;
 #pragma unroll
                         for (int i = 0; i < D; ++i) a0[i] += yv * SL.a[k][i];
                     }
                 }
                 for (int m = 0; m < L.no; ++m) {
-                    const T yv = yb[(long long)(FR + m) * P];
+                    const T yv = pw[(FR + m) * 32];
                     T c[D], cr = T(0), c2 = T(0);
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
@@ -219,8 +252,9 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                     stg[2 * FO * BT + o] = yv;
                     stg[3 * FO * BT + o] = rho_p * Dm * yv * yv;
                 }
-                SL.ybg = yb[(long long)(FR + FO) * P];
+                SL.ybg = pw[(FR + FO) * 32];
                 del0 += SL.ybg;
+                prefetch(j + W);  // the buffer is free again
             } else {
                 for (int g = 0; g < ng; ++g) {
                     const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
@@ -581,9 +615,9 @@ cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
 }
 
 template <typename T, int D>
-size_t pair_smem(int W, int mode, int solver, int FO) {
+size_t pair_smem(int W, int mode, int solver, int FR, int FO) {
     size_t b = 0;
-    if (solver == 1) b += (size_t)4 * FO * 32 * W * sizeof(T);
+    if (solver == 1) b += (size_t)4 * FO * 32 * W * sizeof(T) + (size_t)W * (FR + FO + 2 + D) * 32 * sizeof(T);
     if (mode == 1) b += (size_t)W * StatDims<D>::NSTAT * 32 * sizeof(T) + (size_t)W * 2 * sizeof(double);
     return b;
 }
@@ -591,7 +625,7 @@ size_t pair_smem(int W, int mode, int solver, int FO) {
 template <typename T, int D, int MODE, int SOLVER, int NR>
 cudaError_t launch_pair_t(const PairArgs<T> &a, int n_tiles, int W, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    const size_t sm = pair_smem<T, D>(W, MODE, SOLVER, a.g.FO);
+    const size_t sm = pair_smem<T, D>(W, MODE, SOLVER, a.g.FR, a.g.FO);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_pair<T, D, MODE, SOLVER, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
