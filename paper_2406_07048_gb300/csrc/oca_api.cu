@@ -1021,7 +1021,10 @@ oca_status oca_scene_create(oca_ctx *ctx, const oca_scene_desc *d, oca_scene **o
     for (int s = 0; s < S; ++s) order[s] = s;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     for (int s : order)
-        for (int k = 0; k < sc->meta[s].ntile; ++k) tl.push_back(Tile{s, 32 * k});
+        for (int k = 0; k < sc->meta[s].ntile; ++k) {
+            const int cols = sc->meta[s].NP * sc->meta[s].N - 32 * k;
+            tl.push_back(Tile{s, 32 * k, cols <= 16 ? 1 : 0});
+        }
     // warps per tile: about 8 obstacles per warp at the median obstacle count
     std::nth_element(Ms.begin(), Ms.begin() + Ms.size() / 2, Ms.end());
     const int Mmed = Ms[Ms.size() / 2];

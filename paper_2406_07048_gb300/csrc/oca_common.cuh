@@ -31,6 +31,7 @@ struct ScenMeta {
 struct Tile {
     int scen;
     int q0;
+    int split;  // a scenario's last tile with <= 16 columns: the pair kernel runs it as half-warps
 };
 
 // Scene geometry as kernels see it.

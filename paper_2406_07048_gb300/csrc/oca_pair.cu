@@ -87,8 +87,14 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
     const int lane = threadIdx.x, warp = threadIdx.y, W = blockDim.y;
     const int BT = 32 * W, tid = warp * 32 + lane;
     const int Q = sm.NP * sm.N;
-    const int q = tile.q0 + lane;
+    // a tail tile of at most 16 columns runs as 2W half-warps over the same
+    // columns: half hh of warp w sweeps obstacles 2w + hh, 2w + hh + 2W, ...
+    // (the face loops then cost the larger of two face counts, not their sum)
+    const bool split = tile.split != 0;
+    const int hh = split ? lane >> 4 : 0;
+    const int q = tile.q0 + (split ? (lane & 15) : lane);
     const bool valid = q < Q;
+    const int j0 = split ? 2 * warp + hh : warp, JS = split ? 2 * W : W;
     const long long P = a.P;
     const int FR = a.g.FR, FO = a.g.FO;
     // shared memory: [staged face data 4 x FO x BT] [next obstacle's pair data W x NPF x 32]
@@ -171,9 +177,9 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                 cp_async_commit();
             }
         };
-        prefetch(warp);
+        prefetch(j0);
 
-        for (int j = warp; j < sm.M; j += W) {
+        for (int j = j0; j < sm.M; j += JS) {
             const int gm = sm.obs0 + j;
             L.C = a.g.obs_C + (long long)gm * FO * D;
             L.d = a.g.obs_d + (long long)gm * FO;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                     for (int m = 0; m < L.no; ++m) y_out[(long long)(FR + m) * P + p] = y_in[(long long)(FR + m) * P + p];
                     y_out[(long long)(FR + FO) * P + p] = y_in[(long long)(FR + FO) * P + p];
                 }
-                prefetch(j + W);
+                prefetch(j + JS);
                 continue;
             }
             T zeta, xi[D];
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                 }
                 SL.ybg = pw[(FR + FO) * 32];
                 del0 += SL.ybg;
-                prefetch(j + W);  // the buffer is free again
+                prefetch(j + JS);  // the buffer is free again
             } else {
                 for (int g = 0; g < ng; ++g) {
                     const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
@@ -455,6 +461,15 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
     if (MODE == 1) {
         // ---- reduce statistics and residual partials across the W warps
         T *rs = red;  // [W][NSTAT][32]
+        if (do_qp && split) {
+            // the upper half's statistics belong to the same columns as the lower half's
+#pragma unroll
+            for (int k = 0; k < NW; ++k) st_W[k] += __shfl_down_sync(0xffffffffu, st_W[k], 16);
+#pragma unroll
+            for (int k = 0; k < D; ++k) st_Wc[k] += __shfl_down_sync(0xffffffffu, st_Wc[k], 16);
+#pragma unroll
+            for (int k = 0; k < D * D; ++k) st_E[k] += __shfl_down_sync(0xffffffffu, st_E[k], 16);
+        }
         if (do_qp) {
 #pragma unroll
             for (int k = 0; k < NW; ++k) rs[(warp * NSTAT + k) * 32 + lane] = st_W[k];
@@ -474,7 +489,7 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
             rr[2 * warp + 1] = rd;
         }
         __syncthreads();
-        if (do_qp && valid) {
+        if (do_qp && valid && hh == 0) {
             for (int k = warp; k < NSTAT; k += W) {
                 T acc = T(0);
                 for (int w2 = 0; w2 < W; ++w2) acc += rs[(w2 * NSTAT + k) * 32 + lane];
