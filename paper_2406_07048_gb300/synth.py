@@ -354,6 +354,26 @@ def config1() -> Scene:
     return _assemble(model, [sc], "plain-2d-bicycle-N20-M4")
 
 
+def config_max() -> Scene:
+    """Sizes at the library's compiled-in maxima next to a minimal scenario
+    (a ragged batch of two): bicycle; scenario 0 has horizon 256, a regular
+    octagonal body (8 faces, inradius 1 m) and 6 obstacles of 24 faces in a
+    120 x 12 m corridor; scenario 1 has horizon 3, the 4.5 x 2 m rectangle
+    and 2 triangles."""
+    model = bicycle_model()
+    rng = np.random.default_rng(11)
+    ang = 2.0 * math.pi * np.arange(8) / 8.0
+    octagon = (np.stack([np.cos(ang), np.sin(ang)], 1), np.ones(8), 0, np.array([1.25, 0.0]))
+    N = 256
+    keep = [np.array([0.0, 6.0]), np.array([120.0, 6.0])]
+    big = _Scen(_place_2d(rng, 6, 24, 24, 0.0, 120.0, 0.0, 12.0, keep, 6.0), [octagon], N,
+                _ref_2d(model, N, 0.0, 120.0, 6.0), np.zeros((N, model.nu)))
+    keep = [np.array([0.0, 5.0]), np.array([3.0, 5.0])]
+    small = _Scen(_place_2d(rng, 2, 3, 3, 0.0, 20.0, 0.0, 10.0, keep, 5.0), [_bicycle_body()], 3,
+                  _ref_2d(model, 3, 0.0, 3.0, 5.0), np.zeros((3, model.nu)))
+    return _assemble(model, [big, small], "max-sizes-2d-bicycle-N256-F24-R8")
+
+
 def _trailer_scen(rng, model, N, n_obs, fmin, fmax, length, width, n_parts, v_ref=10.0):
     """Obstacles over length x width; the reference runs along the centre line
     at v_ref (the horizon covers min(length, v_ref N dt) of it)."""

@@ -341,3 +341,80 @@ def test_admm_y_padding_untouched(B, ctx, iters):
     ref.solve(max_iter=iters, eps_pri=0.0, eps_dual=0.0)
     assert np.array_equal(y[~pad], ds.to_host_pairs(ref.y)[~pad])
     ds.close()
+
+
+def test_maximum_sizes(B, ctx, ora):
+    """The compiled-in maxima (24 obstacle faces, 8 part faces, horizon 256)
+    next to a horizon-3 scenario: scale LPs, pair QPs (prox 1: y unique;
+    prox 0: objective) and five FP64 ADMM iterations against the oracle."""
+    sc = synth.config_max()
+    assert sc.fo_max == 24 and sc.fr_max == 8 and int(sc.horizon.max()) == 256
+    rng = np.random.default_rng(5)
+    states = synth.random_states(sc, rng, 2.0, 0.5)
+    for dtype in (F64, F32):
+        ds = B.DeviceScene(ctx, sc, dtype)
+        out = B.scale_detect(ds, ds.tensor(states))
+        ref = ora.scale_batch(sc, states)
+        a_g = out["alpha"].double().cpu().numpy()
+        err = np.abs(a_g - ref["alpha"]) / np.maximum(1.0, np.abs(ref["alpha"]))
+        assert err.max() <= (1e-9 if dtype == F64 else 1e-4), err.max()
+        far = np.abs(ref["alpha"] - 1.0) > 1e-3
+        assert (out["verdict"].cpu().numpy().astype(bool)[far] == (ref["alpha"][far] >= 1.0)).all()
+        st, zeta, xi, y = _qp_inputs(sc, rng, True)
+        for prox in (1.0, 0.0):
+            q = B.pair_qp(ds, ds.tensor(st), ds.tensor(zeta), ds.to_device_pairs(xi), ds.to_device_pairs(y),
+                          prox=prox)
+            rq = ora.pair_qp_batch(sc, st, zeta, xi, y, prox=prox)
+            ok = (q["status"].cpu().numpy() == 0) & (rq["status"] == 0)
+            assert ok.mean() >= 0.999
+            o_g = q["obj"].double().cpu().numpy()
+            e = np.abs(o_g - rq["obj"]) / np.maximum(1.0, rq["obj"])
+            assert e[ok].max() <= (1e-9 if dtype == F64 else 1e-4), (prox, e[ok].max())
+            if prox > 0:
+                yg = ds.to_host_pairs(q["y"])
+                ye = np.abs(yg - rq["y"]).max(axis=1) / np.maximum(1.0, np.abs(rq["y"]).max(axis=1))
+                assert ye[ok].max() <= (1e-7 if dtype == F64 else 5e-3), ye[ok].max()
+        ds.close()
+    ds, pb, rep, ref = _admm_both(B, ctx, ora, sc, F64, max_iter=5, eps_pri=0.0, eps_dual=0.0)
+    assert (rep["iters"].cpu().numpy() == 5).all() and (ref["iters"] == 5).all()
+    assert np.abs(pb.s.cpu().numpy() - ref["s"]).max() < 1e-7 * (1 + np.abs(ref["s"]).max())
+    assert np.abs(pb.zeta.cpu().numpy() - ref["zeta"]).max() < 1e-7 * (1 + np.abs(ref["zeta"]).max())
+
+
+def test_scene_validation_errors(B, ctx):
+    """oca_scene_create refuses what the header rules out, with its codes:
+    OCA_ERR_INVALID_ARGUMENT (1) for an empty batch, a scenario without
+    obstacles, a zero horizon, face counts outside 1..fo_max or below dim+1
+    for a part, a bad link; OCA_ERR_CAPACITY (5) beyond the compiled-in
+    maxima (horizon 256, 24 obstacle faces)."""
+    import ctypes as C
+    import dataclasses
+    base = synth.config1()
+
+    def code_of(sc):
+        with pytest.raises(B.OcaError) as e:
+            B.DeviceScene(ctx, sc, F64)
+        return e.value.code
+
+    def with_(field, idx, value):
+        arr = getattr(base, field).copy()
+        arr[idx] = value
+        return dataclasses.replace(base, **{field: arr})
+
+    assert code_of(with_("horizon", 0, 0)) == 1
+    assert code_of(with_("horizon", 0, 257)) == 5
+    assert code_of(with_("obs_nf", 0, 0)) == 1
+    assert code_of(with_("obs_nf", 0, base.fo_max + 1)) == 1
+    assert code_of(with_("part_nf", 0, 2)) == 1
+    assert code_of(with_("part_link", 0, 2)) == 1
+    assert code_of(with_("obs_begin", 1, 0)) == 1  # a scenario with no obstacle
+    wide = dataclasses.replace(base, obs_C=np.pad(base.obs_C, ((0, 0), (0, 25 - base.fo_max), (0, 0))),
+                               obs_d=np.pad(base.obs_d, ((0, 0), (0, 25 - base.fo_max)), constant_values=1.0))
+    assert code_of(wide) == 5
+    # an empty batch, through the raw descriptor of a valid scene
+    ds = B.DeviceScene(ctx, base, F64)
+    d = B.SceneDesc.from_buffer_copy(ds.desc)
+    d.n_scen = 0
+    h = C.c_void_p()
+    assert B.lib().oca_scene_create(ctx.h, C.byref(d), C.byref(h)) == 1
+    ds.close()
