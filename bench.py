@@ -223,6 +223,8 @@ def gpu_arm(args):
     clk = clocks.stop()
 
     qp_solves, converged, algo_bytes, pair_units = 0.0, 0, 0.0, 0.0
+    ric_stages = 0.0                                   # Riccati stages the trajectory kernel factorised
+    hz = scene.horizon.astype(np.float64)
     iters_all = []
     d1 = scene.dim + 1
     ny_sum = (bpp / 4 - 2 * d1 * pc) / 2               # sum over a scenario's pairs of n_y
@@ -241,6 +243,7 @@ def gpu_arm(args):
         n_full = np.where(capped, np.maximum(it - 1, 0), it)
         algo_bytes += float((b_first + n_full * b_full + capped * b_head).sum())
         pair_units += float((pc * (it + 1)).sum())
+        ric_stages += float((hz * it).sum())
     tot = np.array([qp_solves, converged, ms, algo_bytes, prof["pair_ms"], prof["traj_ms"], prof["pair_launches"],
                     pair_units], dtype=np.float64)
     if dist:
@@ -341,6 +344,17 @@ def gpu_arm(args):
     }
     if clk:
         out["clocks"] = clk
+    if rank == 0 and prof["traj_ms"] > 0:
+        # trajectory kernel against the measured FP64 rate: algorithmic FP64
+        # flops of its backward recursion and forward sweep per stage
+        fp64 = binding.fp64_peak(local)
+        f_stage = ric_flops_per_stage(scene.model.ns, scene.model.nu)
+        ach = f_stage * ric_stages / (prof["traj_ms"] / 1e3) / 1e9
+        out["roofline_trajectory"] = {
+            "bound": "fp64", "achieved": ach, "peak": fp64, "unit": "GFLOP/s", "frac": ach / fp64 if fp64 > 0 else None,
+            "kernel": "k_riccati (FP64 backward Riccati recursion + forward sweep; the FP32 stage assembly not counted)",
+            "flops_per_stage": f_stage, "stages": ric_stages,
+            "peak_source": "measured on this GPU (oca_fp64_peak: FP64 FMA microbenchmark)"}
     if rank == 0 and not args.no_lemke:
         out["pair_solver_comparison"] = solver_comparison(ds, s0, y0, params)
     if rank == 0 and args.closed_loop > 0:
@@ -381,6 +395,18 @@ def solver_comparison(ds, s0, y_cold, params):
     res["workload"] = f"step 1 of the first ADMM iteration, {ds.n_pairs} pairs, prox {prox}, FP32 (launch includes poses)"
     res["speedup"] = res["lemke"]["ms_per_launch"] / res["semismooth_newton"]["ms_per_launch"]
     return res
+
+
+def ric_flops_per_stage(ns: int, nu: int) -> int:
+    """FP64 flops (2 per FMA) of one stage of the trajectory kernel's backward
+    recursion and forward sweep: Y = P [A | B | c] (ns x (ns+nu+1), ns terms
+    each), the upper triangle and gradient column of the stage matrix (ns
+    terms each), [K | k] = -Quu^-1 [Qus | qu], the upper triangle of P and p,
+    then u = K s + k and s' = A s + B u + c."""
+    nx, nz = ns + nu + 1, ns + nu
+    fma = (ns * nx * ns + (nz * (nz + 1) // 2 + nz) * ns + nu * (ns + 1) * nu
+           + (ns * (ns + 1) // 2 + ns) * nu + nu * ns + ns * nz)
+    return 2 * fma
 
 
 def closed_loop(ctx, args, params, with_oracle):

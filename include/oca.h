@@ -404,6 +404,16 @@ typedef struct {
 oca_status oca_profile_enable(oca_ctx *ctx, int enable);
 oca_status oca_profile_read(const oca_ctx *ctx, oca_profile_stats *out);
 
+/* FP64 FMA throughput of `device` in GFLOP/s (*gflops), measured by a
+ * synthetic kernel: 2,048 threads per SM, each advancing 8 independent FMA
+ * chains for 8,192 steps; the best of three timed launches after one warm-up
+ * (about 0.1 s in all).  The denominator of the trajectory kernel's FP64
+ * roofline.  Synchronous; allocates 8 bytes and two events and frees them;
+ * the calling thread's current device is restored.
+ * Errors: OCA_ERR_INVALID_ARGUMENT (gflops == NULL, no such device),
+ * OCA_ERR_CUDA. */
+oca_status oca_fp64_peak(int device, double *gflops);
+
 #ifdef __cplusplus
 }
 #endif

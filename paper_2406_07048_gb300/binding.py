@@ -76,7 +76,7 @@ EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create"
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
             "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
             "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward",
-            "oca_mpc_run", "oca_pair_qp_lemke_batch", "oca_admm_fixed_point_tape_bytes"]
+            "oca_mpc_run", "oca_pair_qp_lemke_batch", "oca_admm_fixed_point_tape_bytes", "oca_fp64_peak"]
 
 
 def lib():
@@ -120,6 +120,8 @@ def lib():
         L.oca_admm_tape_bytes.restype = I
         L.oca_admm_fixed_point_tape_bytes.argtypes = [P, C.POINTER(ModelC), C.POINTER(C.c_int64)]
         L.oca_admm_fixed_point_tape_bytes.restype = I
+        L.oca_fp64_peak.argtypes = [I, C.POINTER(C.c_double)]
+        L.oca_fp64_peak.restype = I
         L.oca_admm_solve_taped.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, P, P, P, P,
                                            C.POINTER(Report), P, C.c_int64, P]
         L.oca_admm_solve_taped.restype = I
@@ -350,6 +352,13 @@ def admm_solve(ds: DeviceScene, s_ref, s, u, y, zeta, xi, sigma=300.0, eps_pri=1
                                           _ptr(u), _ptr(y), _ptr(zeta), _ptr(xi), C.byref(rep), _ptr(tape),
                                           C.c_int64(tape.numel()), _stream(stream)), "oca_admm_solve_taped")
     return rep_t
+
+
+def fp64_peak(device: int = 0) -> float:
+    """oca_fp64_peak: measured FP64 FMA throughput (GFLOP/s)."""
+    g = C.c_double(0.0)
+    _check(lib().oca_fp64_peak(int(device), C.byref(g)), "oca_fp64_peak")
+    return float(g.value)
 
 
 def tape_bytes(ds: DeviceScene, max_iter: int, fixed_point: bool = False) -> int:
