@@ -281,28 +281,29 @@ __device__ __forceinline__ bool spd_inverse(const F (&U)[NU][NU], F (&X)[NU][NU]
         X[0][1] = X[1][0] = -U[0][1] * id;
         return true;
     } else {
-        // Cholesky U = L L^T with reciprocal diagonal, then X = L^-T L^-1
-        F L[NU][NU], il[NU];
+        // U = L D L^T (L unit lower triangular: no square roots on the
+        // dependent chain), then X = L^-T D^-1 L^-1; U is positive definite
+        // iff every pivot d_c is positive
+        F L[NU][NU], dg[NU], idg[NU];
         bool ok = true;
 #pragma unroll
         for (int c = 0; c < NU; ++c) {
-            F dg = U[c][c];
+            F dc = U[c][c];
 #pragma unroll
-            for (int k = 0; k < c; ++k) dg -= L[c][k] * L[c][k];
-            ok &= dg > F(0);
-            dg = dg > F(0) ? dg : F(1);
-            const F sq = m_sqrt(dg);
-            il[c] = F(1) / sq;
-            L[c][c] = sq;
+            for (int k = 0; k < c; ++k) dc -= L[c][k] * L[c][k] * dg[k];
+            ok &= dc > F(0);
+            dc = dc > F(0) ? dc : F(1);
+            dg[c] = dc;
+            idg[c] = F(1) / dc;
 #pragma unroll
             for (int r = c + 1; r < NU; ++r) {
                 F acc = U[r][c];
 #pragma unroll
-                for (int k = 0; k < c; ++k) acc -= L[r][k] * L[c][k];
-                L[r][c] = acc * il[c];
+                for (int k = 0; k < c; ++k) acc -= L[r][k] * L[c][k] * dg[k];
+                L[r][c] = acc * idg[c];
             }
         }
-        // Z = L^-1 (lower triangular)
+        // Z = L^-1 (unit lower triangular)
         F Z[NU][NU];
 #pragma unroll
         for (int c = 0; c < NU; ++c)
@@ -311,12 +312,12 @@ __device__ __forceinline__ bool spd_inverse(const F (&U)[NU][NU], F (&X)[NU][NU]
                 if (r < c) {
                     Z[r][c] = F(0);
                 } else if (r == c) {
-                    Z[r][c] = il[r];
+                    Z[r][c] = F(1);
                 } else {
                     F acc = F(0);
 #pragma unroll
                     for (int k = c; k < r; ++k) acc -= L[r][k] * Z[k][c];
-                    Z[r][c] = acc * il[r];
+                    Z[r][c] = acc;
                 }
             }
 #pragma unroll
@@ -325,7 +326,7 @@ __device__ __forceinline__ bool spd_inverse(const F (&U)[NU][NU], F (&X)[NU][NU]
             for (int j = 0; j <= i; ++j) {
                 F acc = F(0);
 #pragma unroll
-                for (int k = 0; k < NU; ++k) acc += Z[k][i] * Z[k][j];
+                for (int k = 0; k < NU; ++k) acc += Z[k][i] * idg[k] * Z[k][j];
                 X[i][j] = X[j][i] = acc;
             }
         return ok;
