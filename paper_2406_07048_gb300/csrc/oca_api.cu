@@ -403,7 +403,7 @@ template <typename T>
 oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr, const void *s_ref, void *s,
                      void *u, void *y, void *zeta, void *xi, const oca_admm_report *rep, cudaStream_t st,
                      void *tape = nullptr, const unsigned char *obs_mask = nullptr,
-                     cudaGraphExec_t *graph_cache = nullptr) {
+                     cudaGraphExec_t *graph_cache = nullptr, bool host_stop = true) {
     k_reset<<<(sc->S + 255) / 256, 256, 0, st>>>(sc->d_status, sc->S, sc->d_iter, sc->d_active);
     OCA_CK(cudaGetLastError());
     const int NS = model_ns(m->kind), NU = m->kind == 2 ? 4 : 2;
@@ -574,6 +574,12 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
     }
     oca_status out = OCA_OK;
     *sc->h_active = sc->S;
+    // host_stop: read the active count after every chunk and stop when no
+    // scenario is left; without it (the closed loop, where some scenario
+    // nearly always runs to the cap) every chunk is enqueued back to back and
+    // chunks after the last retirement exit at once on the device.  Profiling
+    // reads its per-chunk events, so it keeps the per-chunk wait.
+    const bool wait_each = host_stop || prof;
     for (long long done = 0; done < n_launch; done += G) {
         if (exec) {
             if (cudaGraphLaunch(exec, st) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
@@ -582,6 +588,7 @@ oca_status admm_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *p
                 if (one_iter(k, done + k) != cudaSuccess) { out = OCA_ERR_CUDA; break; }
             if (out != OCA_OK) break;
         }
+        if (!wait_each) continue;
         if (cudaMemcpyAsync(sc->h_active, sc->d_active, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             out = OCA_ERR_CUDA;
@@ -819,7 +826,7 @@ oca_status mpc_impl(oca_scene *sc, const oca_model *m, const oca_admm_params *pr
             out = OCA_ERR_CUDA;
             break;
         }
-        out = admm_impl<T>(sc, m, pr, s_ref, s, u, y, zeta, xi, &rep, st, nullptr, sc->d_mask, &graph);
+        out = admm_impl<T>(sc, m, pr, s_ref, s, u, y, zeta, xi, &rep, st, nullptr, sc->d_mask, &graph, false);
         if (out == OCA_OK && (launch_mpc<T>(a, 2, sc->S, max_blk, st) != cudaSuccess ||
                               launch_mpc<T>(a, 3, sc->S, max_blk, st) != cudaSuccess))
             out = OCA_ERR_CUDA;
