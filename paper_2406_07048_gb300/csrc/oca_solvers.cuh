@@ -894,7 +894,8 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
     }
     // threshold tau: on the active set {t_j >= tau}, sum b z - tau sum b^2/D = 1;
     // the active set is the largest {t_j >= t_k} whose tau stays below t_k
-    T tau = T(0);
+    // (s2 > 0, so tau_k < t_k is tested as s1 - 1 < t_k s2; one division at the end)
+    T bs1 = T(1), bs2 = T(1);
     int best_n = -1;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -908,12 +909,13 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
                 ++n;
             }
         }
-        const T tc = (s1 - T(1)) / s2;
-        if (k < L.nr && tc < t[k] && n > best_n) {
+        if (k < L.nr && s1 - T(1) < t[k] * s2 && n > best_n) {
             best_n = n;
-            tau = tc;
+            bs1 = s1;
+            bs2 = s2;
         }
     }
+    const T tau = (bs1 - T(1)) / bs2;  // 0 when no candidate qualified
     T half_pen = T(0), lin = T(0), lmag = T(0), mag = T(0);
     T a1[D], sc[D], sd = T(0);
 #pragma unroll
