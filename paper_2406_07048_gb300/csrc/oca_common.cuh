@@ -81,6 +81,22 @@ OCA_HD inline float m_tan(float x) { return tanf(x); }
 OCA_HD inline double m_tan(double x) { return tan(x); }
 OCA_HD inline float m_sqrt(float x) { return sqrtf(x); }
 OCA_HD inline double m_sqrt(double x) { return sqrt(x); }
+// 1 / sqrt(x): the hardware-approximated reciprocal square root on the device
+// (within a few ulp; used where only a search direction depends on it)
+OCA_HD inline float m_rsqrt(float x) {
+#ifdef __CUDA_ARCH__
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+OCA_HD inline double m_rsqrt(double x) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
 OCA_HD inline float m_abs(float x) { return fabsf(x); }
 OCA_HD inline double m_abs(double x) { return fabs(x); }
 template <typename T> OCA_HD inline T m_eps();

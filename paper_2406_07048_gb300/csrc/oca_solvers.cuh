@@ -85,16 +85,22 @@ OCA_HD inline void world_dir(const Lane<T, D> &L, const T v[D + 1], T u[D]) {
 // lower-triangular-used, overwritten.  Returns false if not positive definite.
 template <typename T, int NMAX>
 OCA_HD inline bool chol_solve(T G[NMAX][NMAX], T r[NMAX], int n, T tiny) {
+    // G = L L^T with the reciprocal of each diagonal entry kept (one
+    // reciprocal square root per column instead of a square root and a
+    // division per use)
+    T il[NMAX];
 #pragma unroll
     for (int a = 0; a < NMAX; ++a) {
+        il[a] = T(0);
         if (a < n) {
             T dgn = G[a][a];
 #pragma unroll
             for (int k = 0; k < NMAX; ++k)
                 if (k < a) dgn -= G[a][k] * G[a][k];
             if (!(dgn > tiny)) return false;
-            dgn = m_sqrt(dgn);
-            G[a][a] = dgn;
+            const T ia = m_rsqrt(dgn);
+            il[a] = ia;
+            G[a][a] = dgn * ia;
 #pragma unroll
             for (int b2 = 0; b2 < NMAX; ++b2) {
                 if (b2 > a && b2 < n) {
@@ -102,7 +108,7 @@ OCA_HD inline bool chol_solve(T G[NMAX][NMAX], T r[NMAX], int n, T tiny) {
 #pragma unroll
                     for (int k = 0; k < NMAX; ++k)
                         if (k < a) acc -= G[b2][k] * G[a][k];
-                    G[b2][a] = acc / dgn;
+                    G[b2][a] = acc * ia;
                 }
             }
         }
@@ -114,7 +120,7 @@ OCA_HD inline bool chol_solve(T G[NMAX][NMAX], T r[NMAX], int n, T tiny) {
 #pragma unroll
             for (int k = 0; k < NMAX; ++k)
                 if (k < a) acc -= G[a][k] * r[k];
-            r[a] = acc / G[a][a];
+            r[a] = acc * il[a];
         }
     }
 #pragma unroll
@@ -124,7 +130,7 @@ OCA_HD inline bool chol_solve(T G[NMAX][NMAX], T r[NMAX], int n, T tiny) {
 #pragma unroll
             for (int k = 0; k < NMAX; ++k)
                 if (k > a && k < n) acc -= G[k][a] * r[k];
-            r[a] = acc / G[a][a];
+            r[a] = acc * il[a];
         }
     }
     return true;
