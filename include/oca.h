@@ -46,7 +46,7 @@ typedef enum {
     OCA_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, dtype or geometry          */
     OCA_ERR_CUDA = 2,             /* a CUDA runtime call failed                    */
     OCA_ERR_NO_MEMORY = 3,        /* device allocation failed (scene creation)     */
-    OCA_ERR_UNSUPPORTED = 4,      /* valid request this build does not implement   */
+    OCA_ERR_UNSUPPORTED = 4,      /* valid request the library does not implement  */
     OCA_ERR_CAPACITY = 5          /* a size exceeds a compiled-in maximum           */
 } oca_status;
 
