@@ -106,7 +106,7 @@ def pair_bytes(scene, itemsize=4):
         m0, m1 = int(scene.obs_begin[s]), int(scene.obs_begin[s + 1])
         p0 = int(scene.part_begin[s])
         nr = scene.part_nf[p0:p0 + NP].sum()
-        ny = (scene.obs_nf[m0:m1].sum() + 1) * NP * N + nr * (m1 - m0) * N   # sum over pairs of n_y
+        ny = (scene.obs_nf[m0:m1].sum() + (m1 - m0)) * NP * N + nr * (m1 - m0) * N   # sum over pairs of n_y
         P = (m1 - m0) * NP * N
         out[s] = itemsize * (2 * (d + 1) * P + 2 * ny)
     return out
