@@ -163,23 +163,6 @@ def gpu_arm(args):
     if args.riccati_f32:
         params["flags"] = binding.OCA_ADMM_RICCATI_F32
 
-    # --- autotune the warps per tile on the step-1 kernel at the initial state
-    tune = {}
-    for w in ((1, 2, 4, 8, 16) if args.warps <= 0 else ()):
-        ds.warps = w
-        for _ in range(2):
-            binding.pair_qp(ds, pb.s, pb.zeta, pb.xi, y0, prox=params["prox"], y_out=pb.y, want_v=False)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(3):
-            binding.pair_qp(ds, pb.s, pb.zeta, pb.xi, y0, prox=params["prox"], y_out=pb.y, want_v=False)
-        e1.record()
-        torch.cuda.synchronize()
-        tune[w] = e0.elapsed_time(e1) / 3
-    best_w = min(tune, key=tune.get) if tune else args.warps
-    ds.warps = best_w
-
     stream = torch.cuda.current_stream()
 
     def reset():
@@ -188,6 +171,24 @@ def gpu_arm(args):
         pb.y.copy_(y0)
         pb.zeta.zero_()
         pb.xi.zero_()
+
+    # --- autotune the warps per tile on the fused pair kernel as the solve runs
+    # it (ADMM mode): its mean launch time over a short solve from the cold start
+    tune = {}
+    short = dict(params, max_iter=8)
+    for w in ((1, 2, 3, 4, 6, 8, 16) if args.warps <= 0 else ()):
+        ds.warps = w
+        reset()
+        pb.solve(**short)  # warm the tile shape
+        reset()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        pb.solve(**short)
+        pr = ctx.profile_read()
+        ctx.profile(False)
+        tune[w] = pr["pair_ms"] / max(pr["pair_launches"], 1)
+    best_w = min(tune, key=tune.get) if tune else args.warps
+    ds.warps = best_w
 
     def step():
         reset()
