@@ -63,6 +63,7 @@ def lib():
             _lib.ora_dynamics.argtypes = [P, P, P, P, P, P]
             _lib.ora_part_pose.argtypes = [P, I, P, P, P, P, P, P]
             _lib.ora_riccati.argtypes = [I, I, I, P, P, P, P, P, P, P, P, P, P]
+            _lib.ora_riccati_scan.argtypes = [I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, I]
             _lib.ora_cert_margin.argtypes = [I, I, P, P, I, P, P, P, P]
             _lib.ora_cert_margin.restype = D
             _lib.ora_scale_batch.argtypes = [P, P, P, P, P, C.c_longlong, P, P, P, P, P, P, P, I]
@@ -201,6 +202,22 @@ def riccati(A, B, c, Q, q, R, r, s0):
     st = lib().ora_riccati(ns, nu, N, _p(A), _p(B), _p(c), _p(Q), _p(q), _p(R), _p(r), _p(s0),
                            _p(s), _p(u))
     return s, u, st
+
+
+def riccati_scan(A, B, c, Q, q, R, r, s0, tree: bool = True):
+    """The same LQ problem as riccati(), by associative composition of its
+    stage relations (tree: log N rounds of pairwise compositions; else right
+    to left).  Returns s, u, the value functions P [N+1][ns][ns], p [N+1][ns]
+    and the status."""
+    A, B, c, Q, q, R, r, s0 = map(_f64, (A, B, c, Q, q, R, r, s0))
+    N, ns, nu = B.shape[0], B.shape[1], B.shape[2]
+    s = np.zeros((N + 1, ns))
+    u = np.zeros((N, nu))
+    P = np.zeros((N + 1, ns, ns))
+    p = np.zeros((N + 1, ns))
+    st = lib().ora_riccati_scan(ns, nu, N, _p(A), _p(B), _p(c), _p(Q), _p(q), _p(R), _p(r), _p(s0),
+                                _p(s), _p(u), _p(P), _p(p), int(bool(tree)))
+    return s, u, P, p, st
 
 
 def pair_gn(model, A, Cw, dd, link, off, s, y_pad, fr_max, fo_max, zeta, xi):

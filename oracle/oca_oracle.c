@@ -20,6 +20,10 @@
  *   ora_part_pose     rho(s), R(s) of Sec. IV-A and their state derivatives.
  *   ora_riccati       the step-2 LQ subproblem (SQP: one QP per iteration,
  *                     Sec. IV-B) by the textbook backward Riccati recursion.
+ *   ora_riccati_scan  the same LQ subproblem in parallel-in-time form: the
+ *                     stage relations of its optimality conditions composed
+ *                     associatively (pairwise, in log N rounds or right to
+ *                     left), giving every stage's value function P_t, p_t.
  *   ora_admm_scenario the three ADMM steps (eqn:ADMM_dual_updates,
  *                     eqn:ADMM_state_updates, eqn:ADMM_residue_updates) and
  *                     the stopping rule of Sec. IV-B, Gauss-Seidel order.
@@ -683,6 +687,221 @@ int ora_riccati(int ns, int nu, int N, const double *A, const double *B, const d
     free(Kg);
     free(kg);
     return ok ? ORA_FAIL : ORA_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 2 in parallel-in-time form (the same LQ problem as ora_riccati).    */
+/* Its optimality conditions, with costate lam_t = dV_t/ds_t and the        */
+/* stationarity u_t = -R_t^-1 (B_t^T lam_{t+1} + r_t), link each stage's     */
+/* state and costate linearly:                                              */
+/*   s_{t+1} = A_t s_t + b_t - C_t lam_{t+1},                                */
+/*   lam_t   = J_t s_t - eta_t + A_t^T lam_{t+1},                            */
+/* with b_t = c_t - B_t R_t^-1 r_t, C_t = B_t R_t^-1 B_t^T, J_t = Q_t,         */
+/* eta_t = -q_t; the terminal condition lam_N = Q_N s_N + q_N is the         */
+/* element (A, b, C, J, eta) = (0, 0, 0, Q_N, -q_N).  Two consecutive        */
+/* relations (1: i -> j, then 2: j -> k) give, on eliminating s_j and lam_j, */
+/* one of the same form, with M = (I + C1 J2)^-1 (invertible: C1, J2 are     */
+/* positive semidefinite) and M^T = (I + J2 C1)^-1:                         */
+/*   A = A2 M A1,  b = A2 M (b1 + C1 eta2) + b2,  C = A2 M C1 A2^T + C2,      */
+/*   J = J1 + A1^T M^T J2 A1,  eta = eta1 + A1^T M^T (eta2 - J2 b1).          */
+/* Elimination is order-free, so the composition is associative: the       */
+/* suffix e_t o ... o e_N, whose A is 0, states lam_t = J s_t - eta, i.e.    */
+/* the value function's P_t = J, p_t = -eta.  tree != 0 forms every suffix  */
+/* in ceil(log2(N+1)) rounds of pairwise compositions (element t takes      */
+/* element t + 2^r); tree == 0 forms them right to left.  The solution then */
+/* follows by the forward rollout u_t = -(R + B^T P B)^-1 (B^T (P (A s + c)   */
+/* + p) + r), s_{t+1} = A s + B u + c with P, p of stage t+1.                 */
+/* P_out [N+1][ns][ns], p_out [N+1][ns] may be NULL.                        */
+/* ------------------------------------------------------------------------ */
+static int ora_lq_compose(int n, const double *e1, const double *e2, double *e) {
+    /* element layout: A [n*n], b [n], C [n*n], J [n*n], eta [n] */
+    const int nn = n * n;
+    const double *A1 = e1, *b1 = e1 + nn, *C1 = b1 + n, *J1 = C1 + nn, *h1 = J1 + nn;
+    const double *A2 = e2, *b2 = e2 + nn, *C2 = b2 + n, *J2 = C2 + nn, *h2 = J2 + nn;
+    double *A = e, *b = e + nn, *C = b + n, *J = C + nn, *h = J + nn;
+    double T[ORA_MAXS * ORA_MAXS], Tt[ORA_MAXS * ORA_MAXS];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double acc = (i == j) ? 1.0 : 0.0, acct = acc;
+            for (int k = 0; k < n; ++k) {
+                acc += C1[i * n + k] * J2[k * n + j];   /* I + C1 J2 */
+                acct += J2[i * n + k] * C1[k * n + j];  /* I + J2 C1 */
+            }
+            T[i * n + j] = acc;
+            Tt[i * n + j] = acct;
+        }
+    /* X = M [A1 | b1 + C1 eta2 | C1 A2^T], column by column */
+    double XA[ORA_MAXS * ORA_MAXS], Xb[ORA_MAXS], XC[ORA_MAXS * ORA_MAXS], col[ORA_MAXS], sol[ORA_MAXS];
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < n; ++i) col[i] = A1[i * n + j];
+        if (ora_gauss_solve(n, T, col, sol)) return -1;
+        for (int i = 0; i < n; ++i) XA[i * n + j] = sol[i];
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += C1[i * n + k] * A2[j * n + k];  /* (C1 A2^T)[i][j] */
+            col[i] = acc;
+        }
+        if (ora_gauss_solve(n, T, col, sol)) return -1;
+        for (int i = 0; i < n; ++i) XC[i * n + j] = sol[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        double acc = b1[i];
+        for (int k = 0; k < n; ++k) acc += C1[i * n + k] * h2[k];
+        col[i] = acc;
+    }
+    if (ora_gauss_solve(n, T, col, Xb)) return -1;
+    /* Y = M^T [J2 A1 | eta2 - J2 b1] */
+    double YJ[ORA_MAXS * ORA_MAXS], Ye[ORA_MAXS];
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += J2[i * n + k] * A1[k * n + j];
+            col[i] = acc;
+        }
+        if (ora_gauss_solve(n, Tt, col, sol)) return -1;
+        for (int i = 0; i < n; ++i) YJ[i * n + j] = sol[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        double acc = h2[i];
+        for (int k = 0; k < n; ++k) acc -= J2[i * n + k] * b1[k];
+        col[i] = acc;
+    }
+    if (ora_gauss_solve(n, Tt, col, Ye)) return -1;
+    for (int i = 0; i < n; ++i) {
+        double ab = b2[i], ah = h1[i];
+        for (int k = 0; k < n; ++k) {
+            ab += A2[i * n + k] * Xb[k];
+            ah += A1[k * n + i] * Ye[k];
+        }
+        b[i] = ab;
+        h[i] = ah;
+        for (int j = 0; j < n; ++j) {
+            double aa = 0.0, ac = C2[i * n + j], aj = J1[i * n + j];
+            for (int k = 0; k < n; ++k) {
+                aa += A2[i * n + k] * XA[k * n + j];
+                ac += A2[i * n + k] * XC[k * n + j];
+                aj += A1[k * n + i] * YJ[k * n + j];
+            }
+            A[i * n + j] = aa;
+            C[i * n + j] = ac;
+            J[i * n + j] = aj;
+        }
+    }
+    return 0;
+}
+
+int ora_riccati_scan(int ns, int nu, int N, const double *A, const double *B, const double *c,
+                     const double *Q, const double *q, const double *R, const double *r,
+                     const double *s0, double *s, double *u, double *P_out, double *p_out, int tree) {
+    if (ns < 1 || ns > ORA_MAXS || nu < 1 || nu > ORA_MAXU || N < 0) return ORA_BAD_INPUT;
+    const int n = ns, nn = ns * ns, es = 3 * nn + 2 * ns, E = N + 1;
+    double *cur = (double *)malloc(sizeof(double) * (size_t)es * E);
+    double *nxt = (double *)malloc(sizeof(double) * (size_t)es * E);
+    int ok = (cur && nxt) ? 0 : -1;
+    /* the stage elements */
+    for (int t = 0; t < E && ok == 0; ++t) {
+        double *e = cur + (size_t)t * es;
+        double *Ae = e, *be = e + nn, *Ce = be + n, *Je = Ce + nn, *he = Je + nn;
+        memcpy(Je, Q + (size_t)t * nn, sizeof(double) * nn);
+        for (int i = 0; i < n; ++i) he[i] = -q[(size_t)t * n + i];
+        if (t == N) {
+            memset(Ae, 0, sizeof(double) * nn);
+            memset(be, 0, sizeof(double) * n);
+            memset(Ce, 0, sizeof(double) * nn);
+            continue;
+        }
+        const double *At = A + (size_t)t * nn, *Bt = B + (size_t)t * n * nu, *Rt = R + (size_t)t * nu * nu;
+        memcpy(Ae, At, sizeof(double) * nn);
+        /* W = R^-1 B^T (nu x n), z = R^-1 r */
+        double W[ORA_MAXU * ORA_MAXS], z[ORA_MAXU], rhs[ORA_MAXU], sol[ORA_MAXU];
+        for (int j = 0; j < n; ++j) {
+            for (int a = 0; a < nu; ++a) rhs[a] = Bt[j * nu + a];
+            if (ora_gauss_solve(nu, Rt, rhs, sol)) { ok = -1; break; }
+            for (int a = 0; a < nu; ++a) W[a * n + j] = sol[a];
+        }
+        if (ok != 0 || ora_gauss_solve(nu, Rt, r + (size_t)t * nu, z)) { ok = -1; break; }
+        for (int i = 0; i < n; ++i) {
+            double acc = c[(size_t)t * n + i];
+            for (int a = 0; a < nu; ++a) acc -= Bt[i * nu + a] * z[a];
+            be[i] = acc;
+            for (int j = 0; j < n; ++j) {
+                double cc = 0.0;
+                for (int a = 0; a < nu; ++a) cc += Bt[i * nu + a] * W[a * n + j];
+                Ce[i * n + j] = cc;
+            }
+        }
+    }
+    /* suffix compositions */
+    if (ok == 0 && tree) {
+        for (int d = 1; d < E && ok == 0; d *= 2) {
+            for (int t = 0; t < E && ok == 0; ++t) {
+                if (t + d < E) ok = ora_lq_compose(n, cur + (size_t)t * es, cur + (size_t)(t + d) * es,
+                                                   nxt + (size_t)t * es);
+                else memcpy(nxt + (size_t)t * es, cur + (size_t)t * es, sizeof(double) * es);
+            }
+            double *sw = cur; cur = nxt; nxt = sw;
+        }
+    } else if (ok == 0) {
+        for (int t = E - 2; t >= 0 && ok == 0; --t) {
+            ok = ora_lq_compose(n, cur + (size_t)t * es, cur + (size_t)(t + 1) * es, nxt);
+            memcpy(cur + (size_t)t * es, nxt, sizeof(double) * es);
+        }
+    }
+    /* value functions and the forward rollout */
+    if (ok == 0) {
+        if (P_out || p_out)
+            for (int t = 0; t < E; ++t) {
+                const double *e = cur + (size_t)t * es;
+                if (P_out) memcpy(P_out + (size_t)t * nn, e + 2 * nn + n, sizeof(double) * nn);
+                if (p_out)
+                    for (int i = 0; i < n; ++i) p_out[(size_t)t * n + i] = -e[3 * nn + n + i];
+            }
+        memcpy(s, s0, sizeof(double) * n);
+        for (int t = 0; t < N && ok == 0; ++t) {
+            const double *e = cur + (size_t)(t + 1) * es;
+            const double *P = e + 2 * nn + n, *mh = e + 3 * nn + n;  /* P_{t+1}; -p_{t+1} */
+            const double *At = A + (size_t)t * nn, *Bt = B + (size_t)t * n * nu, *ct = c + (size_t)t * n;
+            const double *x = s + (size_t)t * n;
+            double y[ORA_MAXS], w[ORA_MAXS], PB[ORA_MAXS * ORA_MAXU];
+            for (int i = 0; i < n; ++i) {
+                double acc = ct[i];
+                for (int k = 0; k < n; ++k) acc += At[i * n + k] * x[k];
+                y[i] = acc;                                   /* A s + c */
+            }
+            for (int i = 0; i < n; ++i) {
+                double acc = -mh[i];
+                for (int k = 0; k < n; ++k) acc += P[i * n + k] * y[k];
+                w[i] = acc;                                   /* P (A s + c) + p */
+                for (int a = 0; a < nu; ++a) {
+                    double pb = 0.0;
+                    for (int k = 0; k < n; ++k) pb += P[i * n + k] * Bt[k * nu + a];
+                    PB[i * nu + a] = pb;
+                }
+            }
+            double Quu[ORA_MAXU * ORA_MAXU], rhs[ORA_MAXU];
+            for (int a = 0; a < nu; ++a) {
+                double acc = r[(size_t)t * nu + a];
+                for (int k = 0; k < n; ++k) acc += Bt[k * nu + a] * w[k];
+                rhs[a] = -acc;
+                for (int b2 = 0; b2 < nu; ++b2) {
+                    double qq = R[(size_t)t * nu * nu + a * nu + b2];
+                    for (int k = 0; k < n; ++k) qq += Bt[k * nu + a] * PB[k * nu + b2];
+                    Quu[a * nu + b2] = qq;
+                }
+            }
+            double *ut = u + (size_t)t * nu;
+            if (ora_gauss_solve(nu, Quu, rhs, ut)) { ok = -1; break; }
+            double *xn = s + (size_t)(t + 1) * n;
+            for (int i = 0; i < n; ++i) {
+                double acc = y[i];
+                for (int a = 0; a < nu; ++a) acc += Bt[i * nu + a] * ut[a];
+                xn[i] = acc;
+            }
+        }
+    }
+    free(cur);
+    free(nxt);
+    return ok == 0 ? ORA_OK : ORA_FAIL;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -84,3 +84,56 @@ def test_riccati_long_horizon_is_lqr(ora):
     P = scipy.linalg.solve_discrete_are(A1, B1, Q1, R1)
     K = np.linalg.solve(R1 + B1.T @ P @ B1, B1.T @ P @ A1)
     assert np.abs(u[0] + K @ s0).max() < 1e-8
+
+
+# ---- parallel-in-time form (ora_riccati_scan) ---------------------------------
+
+@pytest.mark.parametrize("ns,nu,N", [(4, 2, 20), (5, 2, 50), (12, 4, 16), (12, 4, 40), (3, 1, 1), (5, 2, 63)])
+def test_riccati_scan_equals_dense_kkt(ora, ns, nu, N):
+    """The associative composition of the stage relations solves the same LQ
+    problem: the dense KKT solution, in both composition orders."""
+    rng = np.random.default_rng(ns * 1000 + N)
+    prob = _rand_lq(rng, N, ns, nu)
+    s_ref, u_ref = _dense_kkt(*prob)
+    for tree in (True, False):
+        s, u, P, p, st = ora.riccati_scan(*prob, tree=tree)
+        assert st == 0
+        assert np.abs(s - s_ref).max() < 1e-8 * (1 + np.abs(s_ref).max())
+        assert np.abs(u - u_ref).max() < 1e-8 * (1 + np.abs(u_ref).max())
+
+
+def test_riccati_scan_orders_agree_and_value_function_is_valid(ora):
+    """Associativity: pairwise rounds and the right-to-left fold give the same
+    value functions; each P_t is symmetric positive semidefinite and equals
+    Q_N at the terminal stage."""
+    rng = np.random.default_rng(17)
+    prob = _rand_lq(rng, 37, 6, 3)
+    _, _, P1, p1, _ = ora.riccati_scan(*prob, tree=True)
+    _, _, P2, p2, _ = ora.riccati_scan(*prob, tree=False)
+    assert np.abs(P1 - P2).max() < 1e-10 * (1 + np.abs(P2).max())
+    assert np.abs(p1 - p2).max() < 1e-10 * (1 + np.abs(p2).max())
+    Q = prob[3]
+    assert np.array_equal(P1[-1], Q[-1]) and np.array_equal(p1[-1], prob[4][-1])
+    for t in range(P1.shape[0]):
+        assert np.abs(P1[t] - P1[t].T).max() < 1e-10 * (1 + np.abs(P1[t]).max())
+        assert np.linalg.eigvalsh(0.5 * (P1[t] + P1[t].T)).min() > -1e-10
+
+
+def test_riccati_scan_costate_is_cost_gradient(ora):
+    """lam_0 = P_0 s_0 + p_0 is the gradient of the optimal cost in s_0: central
+    differences of the dense KKT optimum (a quadratic in s_0, so exact up to
+    rounding)."""
+    rng = np.random.default_rng(23)
+    A, B, c, Q, q, R, r, s0 = _rand_lq(rng, 12, 4, 2)
+
+    def cost(x0):
+        s, u = _dense_kkt(A, B, c, Q, q, R, r, x0)
+        return (sum(0.5 * s[t] @ Q[t] @ s[t] + q[t] @ s[t] for t in range(len(s)))
+                + sum(0.5 * u[t] @ R[t] @ u[t] + r[t] @ u[t] for t in range(len(u))))
+
+    _, _, P, p, st = ora.riccati_scan(A, B, c, Q, q, R, r, s0)
+    assert st == 0
+    h = 1e-4
+    g = np.array([(cost(s0 + h * e) - cost(s0 - h * e)) / (2 * h) for e in np.eye(len(s0))])
+    lam = P[0] @ s0 + p[0]
+    assert np.abs(g - lam).max() < 1e-6 * (1 + np.abs(lam).max())
