@@ -215,3 +215,35 @@ def qp_kkt_residual(K, kappa, bq, y, prox=0.0, ybar=None):
     viol = [abs(kappa @ y - 1.0), max(0.0, -y.min()), max(0.0, -s.min())]
     viol.append(np.max(np.abs(s * y)))
     return max(viol)
+
+
+# ----------------------------------------------------------------------------
+# certificate-margin pins (Sec. III-B weak duality)
+# ----------------------------------------------------------------------------
+
+def polytope_vertices(A, b):
+    """Vertices of the bounded polytope {x: A x <= b} in 2-D or 3-D: every
+    choice of dim faces whose normals are independent meets in one point;
+    the feasible such points are the vertices."""
+    dim = A.shape[1]
+    out = []
+    for S in itertools.combinations(range(len(b)), dim):
+        M = A[list(S)]
+        if abs(np.linalg.det(M)) < 1e-12:
+            continue
+        x = np.linalg.solve(M, b[list(S)])
+        if np.all(A @ x <= b + 1e-9 * (1.0 + np.abs(b))):
+            out.append(x)
+    return np.array(out)
+
+
+def random_certificate(rng, nr, no, kind):
+    """Nonnegative (lambda, mu) that are in general NOT optimal: independent
+    exponential draws, a sparse draw, or large multipliers."""
+    if kind == 0:
+        return rng.exponential(1.0, nr), rng.exponential(1.0, no)
+    if kind == 1:
+        lam = rng.exponential(1.0, nr) * (rng.uniform(size=nr) < 0.5)
+        lam[rng.integers(nr)] += 0.5
+        return lam, rng.exponential(2.0, no) * (rng.uniform(size=no) < 0.4)
+    return rng.exponential(0.1, nr), rng.exponential(10.0, no)
