@@ -133,6 +133,142 @@ def reduce_over_ranks(tot, dist, device):
     return out
 
 
+class Workload:
+    """One FP32 workload resident on the GPU: the scene, its ADMM state at
+    the cold start, and the benchmark step (solve + checks)."""
+
+    def __init__(self, ctx, scene, params, warps=0):
+        import torch
+
+        from paper_2406_07048_gb300 import binding
+        self.torch, self.binding = torch, binding
+        self.scene, self.params = scene, params
+        self.ds = binding.DeviceScene(ctx, scene, torch.float32)
+        self.pb = binding.Problem(self.ds)
+        self.s0, self.u0, self.y0 = self.pb.s.clone(), self.pb.u.clone(), self.pb.y.clone()
+        # tile shape: the library's tuner times the fused pair kernel of short
+        # solves from the cold start for each candidate
+        self.tune = self.ds.autotune_warps(self.pb, params) if warps <= 0 else {}
+        if warps > 0:
+            self.ds.warps = warps
+
+    def reset(self):
+        pb = self.pb
+        pb.s.copy_(self.s0)
+        pb.u.copy_(self.u0)
+        pb.y.copy_(self.y0)
+        pb.zeta.zero_()
+        pb.xi.zero_()
+
+    def step(self, **over):
+        """One step: the whole ADMM solve from the cold start, then the scale-LP
+        collision check of the returned plan (Sec. III-A) and the FP64
+        certificate margin of the returned duals (Sec. III-B)."""
+        B, pb, FR, FO = self.binding, self.pb, self.scene.fr_max, self.scene.fo_max
+        self.reset()
+        rep = pb.solve(**dict(self.params, **over))
+        sd = B.scale_detect(self.ds, pb.s, want_certificate=False, want_margin=False)
+        margin = B.cert_margin(self.ds, pb.s, pb.y[:FR], pb.y[FR:FR + FO])
+        return rep, sd, margin
+
+
+def time_workload(wl, steps, warmup, device, dist=None, clocks=None):
+    """Warm-up, then `steps` timed steps with kernel timing on; returns the
+    per-rank totals and per-step reports."""
+    torch = wl.torch
+    for _ in range(warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    ctx = wl.ds.ctx
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = []
+    for _ in range(steps):
+        rep, sd, margin = wl.step()
+        reps.append({k: v.clone() for k, v in rep.items()})
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    return ms, prof, reps, clk, margin
+
+
+def solve_totals(scene, reps, itemsize=4):
+    """Pair-QP solves (all, and of converged scenarios only), converged
+    scenarios, algorithmic bytes of every pair-kernel launch, pair units and
+    Riccati stages of a list of per-step reports."""
+    bpp = pair_bytes(scene, itemsize)
+    pc = scene.pair_counts.astype(np.float64)
+    hz = scene.horizon.astype(np.float64)
+    d1 = scene.dim + 1
+    ny_sum = (bpp / itemsize - 2 * d1 * pc) / 2          # sum over a scenario's pairs of n_y
+    b_first = itemsize * (d1 * pc + 2 * ny_sum)          # j = 0: zeta, xi read; y read and written
+    b_full = itemsize * (2 * d1 * pc + 2 * ny_sum)       # dual update + QP: zeta, xi, y read and written
+    b_head = itemsize * (2 * d1 * pc + ny_sum)           # dual update only (j = max_iter)
+    t = dict(qp=0.0, qp_conv=0.0, conv=0, bytes=0.0, units=0.0, stages=0.0, iters=[])
+    for rep in reps:
+        it = rep["iters"].cpu().numpy().astype(np.float64)
+        st = rep["status"].cpu().numpy()
+        t["qp"] += float((pc * it).sum())
+        t["qp_conv"] += float((pc * it)[st == 0].sum())
+        t["conv"] += int((st == 0).sum())
+        t["iters"].append(it)
+        # a scenario retired at check j ran launches 0..j; one that reached
+        # max_iter ran 0..max_iter-1 in full and a dual-update-only launch
+        capped = st == 1
+        n_full = np.where(capped, np.maximum(it - 1, 0), it)
+        t["bytes"] += float((b_first + n_full * b_full + capped * b_head).sum())
+        t["units"] += float((pc * (it + 1)).sum())
+        t["stages"] += float((hz * it).sum())
+    return t
+
+
+def iteration_histogram(iters, max_iter):
+    edges = [0, 25, 50, 100, 150, 200, 250, max_iter, max_iter + 1]
+    edges = sorted(set(e for e in edges if e <= max_iter + 1))
+    h = np.histogram(np.concatenate(iters), bins=edges)[0]
+    return {"edges": edges, "counts": h.tolist()}
+
+
+def issue_fraction(prof_pair_ms, pair_units, n_sm, sm_mhz):
+    """FP32-issue side of the pair kernel's roofline: warp instructions per
+    pair-iteration from the committed ncu counters of the current kernel
+    sources, times the pair-iterations of the timed launches, over their
+    event time, against 4 warp-instruction issue slots per SM per clock."""
+    kv = _read_kv(os.path.join(ROOT, "profiles", "k_pair_traffic.txt"))
+    if kv.get("kernel_sha") != _kernel_sha() or "warp_inst_per_pair" not in kv or prof_pair_ms <= 0:
+        return None
+    achieved = float(kv["warp_inst_per_pair"]) * pair_units / (prof_pair_ms / 1e3)
+    peak = n_sm * 4 * sm_mhz * 1e6
+    return {"achieved_warp_inst_per_s": achieved, "peak_warp_inst_per_s": peak, "frac": achieved / peak,
+            "warp_inst_per_pair": float(kv["warp_inst_per_pair"]),
+            "lanes_per_inst": float(kv["lanes_per_inst"]) if "lanes_per_inst" in kv else None,
+            "source": "ncu smsp__inst_executed.sum of the current kernel (profiles/k_pair_traffic.txt); "
+                      f"peak = {n_sm} SMs x 4 issue slots x {sm_mhz:.0f} MHz (median SM clock of the timed region)"}
+
+
+def _read_kv(path):
+    kv = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    kv[k] = v
+    return kv
+
+
 def gpu_arm(args):
     import torch
 
@@ -152,9 +288,6 @@ def gpu_arm(args):
     S = args.scen
     scene = synth.config3(n_scen=S, first=shard_first(rank, S))
     ctx = binding.Context(local)
-    ds = binding.DeviceScene(ctx, scene, torch.float32)
-    pb = binding.Problem(ds)
-    s0, u0, y0 = pb.s.clone(), pb.u.clone(), pb.y.clone()
     params = dict(binding.DEFAULTS)
     params["max_iter"] = args.max_iter
     for k in ("prox", "damp"):
@@ -162,99 +295,31 @@ def gpu_arm(args):
             params[k] = getattr(args, k)
     if args.riccati_f32:
         params["flags"] = binding.OCA_ADMM_RICCATI_F32
+    wl = Workload(ctx, scene, params, args.warps)
+    pb, ds = wl.pb, wl.ds
 
-    stream = torch.cuda.current_stream()
-
-    def reset():
-        pb.s.copy_(s0)
-        pb.u.copy_(u0)
-        pb.y.copy_(y0)
-        pb.zeta.zero_()
-        pb.xi.zero_()
-
-    # --- autotune the warps per tile on the fused pair kernel as the solve runs
-    # it (ADMM mode): its mean launch time over a short solve from the cold start
-    tune = {}
-    short = dict(params, max_iter=8)
-    for w in ((1, 2, 3, 4, 6, 8, 16) if args.warps <= 0 else ()):
-        ds.warps = w
-        reset()
-        pb.solve(**short)  # warm the tile shape
-        reset()
-        torch.cuda.synchronize()
-        ctx.profile(True)
-        pb.solve(**short)
-        pr = ctx.profile_read()
-        ctx.profile(False)
-        tune[w] = pr["pair_ms"] / max(pr["pair_launches"], 1)
-    best_w = min(tune, key=tune.get) if tune else args.warps
-    ds.warps = best_w
-
-    def step():
-        reset()
-        rep = pb.solve(**params)
-        sd = binding.scale_detect(ds, pb.s, want_certificate=False, want_margin=False)
-        return rep, sd
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    bpp = pair_bytes(scene)
-    pc = scene.pair_counts.astype(np.float64)
     clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ctx.profile(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    reps = []
-    for _ in range(args.steps):
-        rep, sd = step()
-        reps.append({k: v.clone() for k, v in rep.items()})
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-
-    qp_solves, converged, algo_bytes, pair_units = 0.0, 0, 0.0, 0.0
-    ric_stages = 0.0                                   # Riccati stages the trajectory kernel factorised
-    hz = scene.horizon.astype(np.float64)
-    iters_all = []
-    d1 = scene.dim + 1
-    ny_sum = (bpp / 4 - 2 * d1 * pc) / 2               # sum over a scenario's pairs of n_y
-    b_first = 4 * (d1 * pc + 2 * ny_sum)               # j = 0: zeta, xi read; y read and written
-    b_full = 4 * (2 * d1 * pc + 2 * ny_sum)            # dual update + QP: zeta, xi, y read and written
-    b_head = 4 * (2 * d1 * pc + ny_sum)                # dual update only (j = max_iter)
-    for rep in reps:
-        it = rep["iters"].cpu().numpy().astype(np.float64)
-        st = rep["status"].cpu().numpy()
-        qp_solves += float((pc * it).sum())
-        converged += int((st == 0).sum())
-        iters_all.append(it)
-        # a scenario retired at check j ran launches 0..j; one that reached
-        # max_iter ran 0..max_iter-1 in full and a dual-update-only launch
-        capped = st == 1
-        n_full = np.where(capped, np.maximum(it - 1, 0), it)
-        algo_bytes += float((b_first + n_full * b_full + capped * b_head).sum())
-        pair_units += float((pc * (it + 1)).sum())
-        ric_stages += float((hz * it).sum())
-    tot = np.array([qp_solves, converged, ms, algo_bytes, prof["pair_ms"], prof["traj_ms"], prof["pair_launches"],
-                    pair_units], dtype=np.float64)
+    ms, prof, reps, clk, margin = time_workload(wl, args.steps, args.warmup, dev, dist, clocks)
+    t = solve_totals(scene, reps)
+    pc = scene.pair_counts.astype(np.float64)
+    tot = np.array([t["qp"], t["conv"], ms, t["bytes"], prof["pair_ms"], prof["traj_ms"], prof["pair_launches"],
+                    t["units"], t["qp_conv"]], dtype=np.float64)
     if dist:
         tot = reduce_over_ranks(tot, dist, dev)
         ms = float(tot[2])
     value = tot[0] / (ms / 1e3)
     admm_rate = tot[1] / (ms / 1e3)
+    m_last = margin.cpu().numpy()
+
+    # --- the same scenarios at a higher iteration cap (untimed): how many
+    # more meet the stopping rule
+    cap2 = max(1000, args.max_iter)
+    rep2, _, _ = wl.step(max_iter=cap2)
+    st2 = rep2["status"].cpu().numpy()
 
     # --- end to end through the public API with host buffers (pinned)
-    h_in = {k: v.cpu().pin_memory() for k, v in dict(s_ref=pb.s_ref, s=s0, u=u0, y=y0, zeta=torch.zeros_like(pb.zeta),
+    h_in = {k: v.cpu().pin_memory() for k, v in dict(s_ref=pb.s_ref, s=wl.s0, u=wl.u0, y=wl.y0,
+                                                      zeta=torch.zeros_like(pb.zeta),
                                                       xi=torch.zeros_like(pb.xi)).items()}
     h_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in dict(s=pb.s, u=pb.u).items()}
     h2d = sum(v.numel() * v.element_size() for v in h_in.values())
@@ -304,20 +369,16 @@ def gpu_arm(args):
     peak, peak_kind = _peaks()
     achieved = tot[3] / (tot[4] / 1e3) / 1e9 if tot[4] > 0 else 0.0
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "k_pair_traffic.txt")
-    if os.path.exists(tp):
-        kv = {}
-        with open(tp) as f:
-            for line in f:
-                if "=" in line and not line.startswith("#"):
-                    k, v = line.strip().split("=", 1)
-                    kv[k] = v
-        if kv.get("kernel_sha") == _kernel_sha() and tot[6] > 0:
-            # measured DRAM bytes per pair, scaled to the pairs an average launch processed
-            traffic = float(kv["dram_bytes_per_pair"]) * tot[7] / tot[6]
-    # per step: reset, 2 box inits, poses, gather, scale-detect poses + LP = 7,
-    # and per iteration launch: pair kernel, trajectory kernel, counter advance
-    launches = int(7 * args.steps * world + 3 * tot[6])
+    kv = _read_kv(os.path.join(ROOT, "profiles", "k_pair_traffic.txt"))
+    if kv.get("kernel_sha") == _kernel_sha() and tot[6] > 0:
+        # measured DRAM bytes per pair, scaled to the pairs an average launch processed
+        traffic = float(kv["dram_bytes_per_pair"]) * tot[7] / tot[6]
+    # per step: reset, 2 box inits, poses, gather, scale-detect poses + LP,
+    # certificate margin = 8, and per iteration launch: pair kernel,
+    # trajectory kernel, counter advance
+    launches = int(8 * args.steps * world + 3 * tot[6])
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -328,36 +389,40 @@ def gpu_arm(args):
                    "scenarios_per_gpu": S, "pairs_per_gpu": int(scene.n_pairs),
                    "admm": {k: params[k] for k in ("sigma", "eps_pri", "eps_dual", "prox", "rho_box", "damp")},
                    "precision": "pair QPs / residuals / duals FP32, Riccati factorisation "
-                                + ("FP32" if args.riccati_f32 else "FP64"),
-                   "warps_per_tile": best_w, "tuner_ms": {str(k): round(v, 4) for k, v in tune.items()},
+                                + ("FP32" if args.riccati_f32 else "FP64") + ", certificate margin FP64",
+                   "step": "whole ADMM solve + scale-LP check + FP64 certificate margin of the returned duals",
+                   "warps_per_tile": ds.warps, "tuner_ms": {str(k): round(v, 4) for k, v in wl.tune.items()},
                    "l2": "inputs larger than L2 (y alone %.0f MB)" % (pb.y.numel() * 4 / 1e6),
                    "parallelism": f"scenario shards x{world}"},
+        "value_counts": "pair-QP solves of every scenario, converged or not (pairs x iterations)",
+        "pair_qp_solves_per_s_converged": tot[8] / (ms / 1e3),
         "admm_solves_per_s": admm_rate,
         "converged_fraction": tot[1] / (S * world * args.steps),
-        "mean_iterations": float(np.mean(np.concatenate(iters_all))),
+        f"converged_fraction_at_{cap2}": float((st2 == 0).mean()),
+        "failed_fraction": float((reps[-1]["status"].cpu().numpy() == 2).mean()),
+        "mean_iterations": float(np.mean(np.concatenate(t["iters"]))),
+        "iteration_histogram": iteration_histogram(t["iters"], args.max_iter),
+        "certified_free_fraction": float((m_last >= 1.0).mean()),
         "kernel_ms": {"pair": tot[4], "trajectory": tot[5], "pair_launches": int(tot[6])},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair (fused dual update + pair QP)",
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                     "issue": issue_fraction(tot[4], tot[7], n_sm, sm_mhz)},
         "e2e": {"value": e_qp / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
         "plain_form": plain,
     }
     if clk:
         out["clocks"] = clk
+    fp64 = binding.fp64_peak(local) if rank == 0 else 0.0
     if rank == 0 and prof["traj_ms"] > 0:
-        # trajectory kernel against the measured FP64 rate: algorithmic FP64
-        # flops of its backward recursion and forward sweep per stage
-        fp64 = binding.fp64_peak(local)
-        f_stage = ric_flops_per_stage(scene.model.ns, scene.model.nu)
-        ach = f_stage * ric_stages / (prof["traj_ms"] / 1e3) / 1e9
-        out["roofline_trajectory"] = {
-            "bound": "fp64", "achieved": ach, "peak": fp64, "unit": "GFLOP/s", "frac": ach / fp64 if fp64 > 0 else None,
-            "kernel": "k_riccati (FP64 backward Riccati recursion + forward sweep; the FP32 stage assembly not counted)",
-            "flops_per_stage": f_stage, "stages": ric_stages,
-            "peak_source": "measured on this GPU (oca_fp64_peak: FP64 FMA microbenchmark)"}
+        out["roofline_trajectory"] = traj_roofline(scene, t["stages"], prof["traj_ms"], fp64)
+    if rank == 0 and args.quad > 0:
+        out["quad"] = quad_workload(ctx, args, params, fp64, world == 1 and not args.no_cpu_baseline, n_sm, sm_mhz)
+    if rank == 0 and args.precision:
+        out["precision_form"] = precision_form(ctx)
     if rank == 0 and not args.no_lemke:
-        out["pair_solver_comparison"] = solver_comparison(ds, s0, y0, params)
+        out["pair_solver_comparison"] = solver_comparison(ds, wl.s0, wl.y0, params)
     if rank == 0 and args.closed_loop > 0:
         out["closed_loop"] = closed_loop(ctx, args, params, world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -366,6 +431,115 @@ def gpu_arm(args):
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def traj_roofline(scene, stages, traj_ms, fp64):
+    """Trajectory kernel against the measured FP64 rate: algorithmic FP64
+    flops of its backward recursion and forward sweep per stage."""
+    f_stage = ric_flops_per_stage(scene.model.ns, scene.model.nu)
+    ach = f_stage * stages / (traj_ms / 1e3) / 1e9
+    return {"bound": "fp64", "achieved": ach, "peak": fp64, "unit": "GFLOP/s", "frac": ach / fp64 if fp64 > 0 else None,
+            "kernel": "k_riccati (FP64 backward Riccati recursion + forward sweep; the FP32 stage assembly not counted)",
+            "flops_per_stage": f_stage, "stages": stages,
+            "peak_source": "measured on this GPU (oca_fp64_peak: FP64 FMA microbenchmark)"}
+
+
+def quad_workload(ctx, args, params, fp64, with_oracle, n_sm, sm_mhz):
+    """The 3-D quadrotor workload (Sec. V-A's vehicle): 64 scenes x 128
+    polyhedra (6-20 faces, half in narrow-gap pairs) x 3 boxes x N = 40,
+    FP32 pair QPs, FP64 Riccati; the same step and metrics as the headline."""
+    from paper_2406_07048_gb300 import synth
+    sc = synth.config4(n_scen=args.quad)
+    wl = Workload(ctx, sc, params, 0)
+    ms, prof, reps, _, margin = time_workload(wl, args.quad_steps, 2, None)
+    t = solve_totals(sc, reps)
+    peak, peak_kind = _peaks()
+    achieved = t["bytes"] / (prof["pair_ms"] / 1e3) / 1e9 if prof["pair_ms"] > 0 else 0.0
+    pb = pair_bytes(sc)
+    out = {"workload": f"3-D quadrotor, {args.quad} scenes x 128 polyhedra (6-20 faces) x 3 boxes x N=40, "
+                       f"cold start, max_iter {params['max_iter']}, FP32 pair QPs, FP64 Riccati",
+           "pairs": int(sc.n_pairs), "steps": args.quad_steps, "ms_per_step": ms / args.quad_steps,
+           "pair_qp_solves_per_s": t["qp"] / (ms / 1e3),
+           "pair_qp_solves_per_s_converged": t["qp_conv"] / (ms / 1e3),
+           "admm_solves_per_s": t["conv"] / (ms / 1e3),
+           "converged_fraction": t["conv"] / (args.quad * args.quad_steps),
+           "mean_iterations": float(np.mean(np.concatenate(t["iters"]))),
+           "certified_free_fraction": float((margin.cpu().numpy() >= 1.0).mean()),
+           "warps_per_tile": wl.ds.warps,
+           "algorithmic_bytes_per_pair_iteration": float(pb.sum() / sc.n_pairs),
+           "kernel_ms": {"pair": prof["pair_ms"], "trajectory": prof["traj_ms"],
+                         "pair_launches": int(prof["pair_launches"])},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "kernel": "k_pair (fused dual update + pair QP)", "traffic": None,
+                        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+           "roofline_trajectory": traj_roofline(sc, t["stages"], prof["traj_ms"], fp64) if prof["traj_ms"] > 0 else None}
+    if with_oracle:
+        import oracle
+        n = min(16, args.quad)
+        sub = synth.subset(sc, list(range(n)))
+        kw = {k: params[k] for k in ("sigma", "eps_pri", "eps_dual", "prox", "rho_box", "damp")}
+        t0 = time.perf_counter()
+        r = oracle.admm_batch(sub, max_iter=20, **kw)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": float((sub.pair_counts * r["iters"]).sum()) / el, "unit": UNIT,
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": f"scenes 0..{n - 1}, the first 20 ADMM iterations, {el:.1f} s"}
+    wl.ds.close()
+    return out
+
+
+def precision_form(ctx):
+    """Precision form (config 2: tractor-trailer, N = 50, 32 obstacles, 3,200
+    pairs, 300 iterations): the FP32 GPU path against the FP64 oracle, error
+    per result.  alpha* and the pair-QP objective are compared on identical
+    inputs (the GPU's final plan and duals, as stored); the trajectory and its
+    cost compare the two whole solves."""
+    import torch
+
+    import oracle
+    from paper_2406_07048_gb300 import binding, synth
+    sc = synth.config2()
+    P = sc.n_pairs
+    ds = binding.DeviceScene(ctx, sc, torch.float32)
+    out = {"workload": f"config 2: 2-D tractor-trailer, N=50, 32 obstacles of 3-12 faces, {P} pairs, 300 iterations"}
+    for K in (10, 300):
+        pb = binding.Problem(ds)
+        rep = pb.solve(max_iter=K)
+        ref = oracle.admm_batch(sc, max_iter=K)
+        s_g = pb.s.double().cpu().numpy()
+        e = np.abs(s_g - ref["s"])
+        c_g, c_o = float(rep["cost"][0]), float(ref["cost"][0])
+        out[f"after_{K}_iterations"] = {
+            "trajectory_max_abs": float(e.max()), "trajectory_median_abs": float(np.median(e)),
+            "cost_rel": abs(c_g - c_o) / abs(c_o), "iters_gpu": int(rep["iters"][0]), "iters_oracle": int(ref["iters"][0]),
+            "r_pri_gpu": float(rep["r_pri"][0]), "r_pri_oracle": float(ref["r_pri"][0]),
+            "r_dual_gpu": float(rep["r_dual"][0]), "r_dual_oracle": float(ref["r_dual"][0])}
+    # per pair on identical inputs: the GPU's final plan (FP32) and duals
+    s32 = pb.s.double().cpu().numpy()
+    sd = binding.scale_detect(ds, pb.s)
+    a_g = sd["alpha"].double().cpu().numpy()
+    a_o = oracle.scale_batch(sc, s32)["alpha"]
+    ea = np.abs(a_g - a_o) / np.maximum(1.0, np.abs(a_o))
+    far = np.abs(a_o - 1.0) > 1e-3
+    v_g = sd["verdict"].cpu().numpy().astype(bool)
+    y = ds.to_host_pairs(pb.y)
+    z = pb.zeta.double().cpu().numpy()
+    x = ds.to_host_pairs(pb.xi)
+    q = binding.pair_qp(ds, pb.s, pb.zeta, pb.xi, pb.y, prox=binding.DEFAULTS["prox"], want_v=True)
+    qo = oracle.pair_qp_batch(sc, s32, z, x, y, prox=binding.DEFAULTS["prox"])
+    o_g = q["obj"].double().cpu().numpy()
+    eo = np.abs(o_g - qo["obj"]) / np.maximum(1.0, np.abs(qo["obj"]))
+    FR, FO = sc.fr_max, sc.fo_max
+    m_g = binding.cert_margin(ds, pb.s, pb.y[:FR], pb.y[FR:FR + FO]).cpu().numpy()
+    out["per_pair"] = {
+        "alpha_rel_max": float(ea.max()), "alpha_rel_median": float(np.median(ea)),
+        "verdicts_identical_where_far_from_1": bool((v_g[far] == (a_o[far] >= 1.0)).all()),
+        "qp_objective_rel_max": float(eo.max()), "qp_objective_rel_median": float(np.median(eo)),
+        "certificate_margin_min": float(m_g.min()),
+        "note": "relative errors floored at 1: |gpu - oracle| / max(1, |oracle|); the pair QP is the step-1 "
+                "QP at the final iterate (prox as the solve)"}
+    ds.close()
+    return out
 
 
 def solver_comparison(ds, s0, y_cold, params):
@@ -568,6 +742,9 @@ def main():
     ap.add_argument("--closed-loop", type=int, default=250, help="control steps of the closed-loop line (0: off)")
     ap.add_argument("--prox", type=float, default=None, help="proximal weight of the pair QP (default: library default)")
     ap.add_argument("--damp", type=float, default=None, help="proximal damping of the trajectory step")
+    ap.add_argument("--quad", type=int, default=64, help="scenes of the quadrotor line (0: off)")
+    ap.add_argument("--quad-steps", type=int, default=3, help="timed steps of the quadrotor line")
+    ap.add_argument("--precision", type=int, default=1, help="precision-form line (config 2 vs the oracle; 0: off)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

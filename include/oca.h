@@ -144,9 +144,14 @@ oca_status oca_scene_info_get(const oca_scene *scene, oca_scene_info *info);
 
 /* Work shape of the pair kernels: warps per 32-lane tile (1..16); each warp
  * sweeps every W-th obstacle of the tile's scenario.  oca_scene_create picks
- * about eight obstacles per warp at the median obstacle count; the tuner in
- * the Python binding times the candidates and sets the fastest.
- * Errors: OCA_ERR_INVALID_ARGUMENT. */
+ * about eight obstacles per warp at the median obstacle count;
+ * DeviceScene.autotune_warps in the Python binding times the fused pair
+ * kernel of short solves for each candidate and sets the fastest.
+ * Errors: OCA_ERR_INVALID_ARGUMENT (warps outside 1..16), OCA_ERR_CAPACITY
+ * (the pair kernels' shared memory for that many warps,
+ * (5 fo_max + fr_max + dim + 2 + nstat) * 32 * warps elements plus 16 bytes per
+ * warp with nstat = 9 in 2-D and 18 in 3-D, exceeds the device's per-block
+ * limit). */
 oca_status oca_scene_set_warps(oca_scene *scene, int warps);
 int oca_scene_get_warps(const oca_scene *scene); /* -1 if scene == NULL */
 
@@ -212,6 +217,26 @@ typedef struct {
 oca_status oca_scale_detect_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
                                   const void *states, void *alpha, void *lambda, void *mu,
                                   double *margin, int32_t *verdict, int32_t *status, void *stream);
+
+/* FP64 certificate margin of caller-given dual variables, per pair
+ * (Sec. III-B, weak duality of eqn:scale_opt / eqn:scale_opt_dual): for any
+ * lambda, mu >= 0,
+ *   alpha* >= -d'^T mu / (b^T lambda + |A^T lambda + C'^T mu| D_R),
+ * D_R the part's largest vertex norm, C' = C R(s_t), d' = d - C rho(s_t).
+ * A margin >= 1 certifies the pair collision-free without solving the LP;
+ * the final check of an ADMM solve passes its returned y (lambda = y,
+ * mu = y + fr_max * P in the padded layout) and states.  The poses are formed
+ * in FP64 from the stored states and every sum is FP64, so the bound holds for
+ * the geometry as stored.
+ * states: [n_states][ns] (scene dtype).  lambda: [fr_max][P], mu: [fo_max][P]
+ * (scene dtype; only a pair's own components are read).  margin: [P] double
+ * out; -DBL_MAX where a component is negative or non-finite, or the
+ * denominator is not positive.
+ * Errors: OCA_ERR_INVALID_ARGUMENT (a NULL pointer, a model that does not
+ * match the scene), OCA_ERR_CUDA. */
+oca_status oca_cert_margin_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model,
+                                 const void *states, const void *lambda, const void *mu, double *margin,
+                                 void *stream);
 
 /* ADMM step 1 alone, Sec. IV-C eqn:const_least_square, per pair:
  *   min 0.5 |K^T y + bq|^2 + 0.5 prox sum_g |K_g|^2 (y_g - y_in,g)^2
@@ -378,6 +403,11 @@ oca_status oca_mpc_run(oca_ctx *ctx, const oca_scene *scene, const oca_model *mo
  * 4 * (M + 2 * n_parts) (rounded up to 256) + (dim + dim^2) * n_parts * N *
  * sizeof(element) must not exceed 1 MiB, else OCA_ERR_CAPACITY; other argument
  * errors give OCA_ERR_INVALID_ARGUMENT before any work is queued.
+ * The host metadata (obs_nf, part_nf, part_link) is copied on `stream` with
+ * cudaMemcpyAsync: from page-locked (pinned) memory the copy stays
+ * asynchronous, and the arrays must then stay valid until it has run on the
+ * stream; from pageable memory the driver stages the data before the call
+ * returns, which can block the calling thread.
  * Every GPU that loads the library holds the 1 MiB until the process exits.
  * The first call on a device looks up the array's device address (make that
  * call before any stream capture); all calls on a device share the array, so

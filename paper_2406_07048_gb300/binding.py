@@ -76,7 +76,8 @@ EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create"
             "oca_scene_info_get", "oca_scene_set_warps", "oca_scene_get_warps", "oca_scale_detect_batch",
             "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
             "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward",
-            "oca_mpc_run", "oca_pair_qp_lemke_batch", "oca_admm_fixed_point_tape_bytes", "oca_fp64_peak"]
+            "oca_mpc_run", "oca_pair_qp_lemke_batch", "oca_admm_fixed_point_tape_bytes", "oca_fp64_peak",
+            "oca_cert_margin_batch"]
 
 
 def lib():
@@ -105,6 +106,8 @@ def lib():
         L.oca_scene_get_warps.restype = I
         L.oca_scale_detect_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, P, P, P, P, P]
         L.oca_scale_detect_batch.restype = I
+        L.oca_cert_margin_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, P, P]
+        L.oca_cert_margin_batch.restype = I
         L.oca_pair_qp_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, D, P, P, P, P, P, P]
         L.oca_pair_qp_batch.restype = I
         L.oca_admm_solve.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, P, P, P, P,
@@ -224,17 +227,76 @@ class DeviceScene:
         d.obs_begin, d.obs_nf, d.part_begin, d.part_nf, d.part_link, d.horizon = [a.ctypes.data for a in self._host]
         d.obs_C, d.obs_d = self.obs_C.data_ptr(), self.obs_d.data_ptr()
         d.part_A, d.part_b, d.part_off = self.part_A.data_ptr(), self.part_b.data_ptr(), self.part_off.data_ptr()
+        self._create(d, dev)
+
+    def _create(self, d: "SceneDesc", dev):
         self.desc = d
         h = C.c_void_p()
-        _check(lib().oca_scene_create(ctx.h, C.byref(d), C.byref(h)), "oca_scene_create")
+        _check(lib().oca_scene_create(self.ctx.h, C.byref(d), C.byref(h)), "oca_scene_create")
         self.h = h
         info = SceneInfo()
         _check(lib().oca_scene_info_get(h, C.byref(info)), "oca_scene_info_get")
         self.n_pairs, self.n_states, self.n_ctrls = info.n_pairs, info.n_states, info.n_ctrls
         self.ny_max, self.n_tiles = info.ny_max, info.n_tiles
-        assert self.n_pairs == scene.n_pairs and self.ny_max == scene.ny_max
-        self.model = model_c(scene.model)
+        assert self.n_pairs == self.scene.n_pairs and self.ny_max == self.scene.ny_max
+        self.model = model_c(self.scene.model)
         self.device = dev
+
+    def with_offsets(self, obs_d: torch.Tensor) -> "DeviceScene":
+        """A second scene over the same device geometry except the obstacle
+        offsets, which are `obs_d` [M_tot, fo_max] (kept alive by the new
+        scene).  It has its own workspace, so solves on it leave this scene
+        and its offsets untouched."""
+        new = DeviceScene.__new__(DeviceScene)
+        new.ctx, new.scene, new.dtype = self.ctx, self.scene, self.dtype
+        new.obs_C, new.part_A, new.part_b, new.part_off = self.obs_C, self.part_A, self.part_b, self.part_off
+        new.obs_d = obs_d.detach().to(self.dtype).contiguous()
+        assert new.obs_d.shape == self.obs_d.shape and new.obs_d.device == self.obs_d.device
+        new._host = self._host
+        d = SceneDesc()
+        for name, _ in SceneDesc._fields_:
+            setattr(d, name, getattr(self.desc, name))
+        d.obs_d = new.obs_d.data_ptr()
+        new._create(d, self.device)
+        new.warps = self.warps
+        return new
+
+    def autotune_warps(self, problem: "Problem", params: Optional[dict] = None,
+                       candidates=(1, 2, 3, 4, 6, 8, 16), iters: int = 8) -> dict:
+        """Choose the warps per tile of the pair kernels by timing the fused
+        pair kernel as the ADMM runs it: for each candidate, a short solve of
+        `iters` iterations from the problem's current state (restored after
+        every trial) with kernel timing on; the candidate with the least mean
+        pair-kernel time per launch is set.  Returns {warps: ms per launch}."""
+        kw = dict(DEFAULTS)
+        kw.update(params or {})
+        kw["max_iter"] = iters
+        saved = [t.clone() for t in (problem.s, problem.u, problem.y, problem.zeta, problem.xi)]
+
+        def restore():
+            for dst, src in zip((problem.s, problem.u, problem.y, problem.zeta, problem.xi), saved):
+                dst.copy_(src)
+
+        times = {}
+        for w in candidates:
+            try:
+                self.warps = w
+            except OcaError as e:
+                if e.code == 5:      # too many warps for the shared memory of this scene's face counts
+                    continue
+                raise
+            restore()
+            problem.solve(**kw)          # first use of this tile shape
+            restore()
+            torch.cuda.synchronize(self.device)
+            self.ctx.profile(True)
+            problem.solve(**kw)
+            pr = self.ctx.profile_read()
+            self.ctx.profile(False)
+            times[w] = pr["pair_ms"] / max(pr["pair_launches"], 1)
+        restore()
+        self.warps = min(times, key=times.get)
+        return times
 
     @property
     def warps(self) -> int:
@@ -283,6 +345,16 @@ def scale_detect(ds: DeviceScene, states: torch.Tensor, want_certificate: bool =
                                         _ptr(mu), _ptr(margin), _ptr(verdict), _ptr(status), _stream(stream)),
            "oca_scale_detect_batch")
     return dict(alpha=alpha, lam=lam, mu=mu, margin=margin, verdict=verdict, status=status)
+
+
+def cert_margin(ds: DeviceScene, states: torch.Tensor, lam: torch.Tensor, mu: torch.Tensor, stream=None):
+    """oca_cert_margin_batch: FP64 weak-duality margin [P] of the given
+    lambda [fr_max, P] and mu [fo_max, P] (e.g. an ADMM solve's y[:fr_max]
+    and y[fr_max:fr_max + fo_max]) at the given states."""
+    margin = torch.empty(ds.n_pairs, dtype=torch.float64, device=ds.device)
+    _check(lib().oca_cert_margin_batch(ds.ctx.h, ds.h, C.byref(ds.model), _ptr(states), _ptr(lam.contiguous()),
+                                       _ptr(mu.contiguous()), _ptr(margin), _stream(stream)), "oca_cert_margin_batch")
+    return margin
 
 
 def scale_detect_noalloc(ds: DeviceScene, states: torch.Tensor, want_certificate: bool = True, stream=None):
@@ -404,33 +476,29 @@ class AdmmCost(torch.autograd.Function):
     as a differentiable function of the obstacle offsets d [M_tot, fo_max]
     and translations delta [M_tot, dim] (the solved obstacle j has offsets
     d_jm + c_jm . delta_j).  Forward: a taped oca_admm_solve from the
-    problem's current state (left unchanged); backward: oca_admm_backward."""
+    problem's current state (left unchanged) on a scene of its own that holds
+    the moved offsets (the problem's scene is not touched); backward:
+    oca_admm_backward on that scene."""
 
     @staticmethod
     def forward(ctx, obs_d, obs_shift, problem, kw):
         ds = problem.ds
         with torch.no_grad():
             d_eff = obs_d + torch.einsum("jmi,ji->jm", ds.obs_C.view(obs_d.shape[0], obs_d.shape[1], -1), obs_shift)
-            saved_d = ds.obs_d.clone()
-            ds.obs_d.copy_(d_eff)
+            dsx = ds.with_offsets(d_eff)
             st = [t.clone() for t in (problem.s, problem.u, problem.y, problem.zeta, problem.xi)]
-            tape = new_tape(ds, kw.get("max_iter", 300))
-            rep = admm_solve(ds, problem.s_ref, *st, tape=tape, **kw)
-        ctx.problem, ctx.kw, ctx.tape, ctx.iters = problem, kw, tape, rep["iters"]
-        ctx.d_eff, ctx.saved_d = d_eff, saved_d
-        ds.obs_d.copy_(saved_d)
+            tape = new_tape(dsx, kw.get("max_iter", 300))
+            rep = admm_solve(dsx, problem.s_ref, *st, tape=tape, **kw)
+        ctx.problem, ctx.kw, ctx.tape, ctx.iters, ctx.scene = problem, kw, tape, rep["iters"], dsx
         return rep["cost"].clone()
 
     @staticmethod
     def backward(ctx, grad_cost):
         problem, kw = ctx.problem, ctx.kw
-        ds = problem.ds
         with torch.no_grad():
-            ds.obs_d.copy_(ctx.d_eff)
             keys = ("sigma", "prox", "max_iter", "rho_box", "damp", "eps_pri", "eps_dual", "flags")
-            g = admm_backward(ds, problem.s_ref, ctx.tape, ctx.iters, grad_cost,
+            g = admm_backward(ctx.scene, problem.s_ref, ctx.tape, ctx.iters, grad_cost,
                               **{k: kw[k] for k in keys if k in kw})
-            ds.obs_d.copy_(ctx.saved_d)
         return g["obs_offset"], g["obs_center"], None, None
 
 

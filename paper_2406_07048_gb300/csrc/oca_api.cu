@@ -16,6 +16,7 @@ using namespace oca;
 struct oca_ctx {
     int device;
     int n_sm;
+    int smem_optin;  // largest dynamic shared memory per block (opt-in), bytes
     // kernel timing (oca_profile_enable)
     bool prof = false;
     cudaEvent_t ev[4][8] = {};  // [pair start, pair stop, traj start, traj stop][iteration in chunk]
@@ -97,6 +98,12 @@ DevModel<T> make_model(const oca_model *m) {
 }
 
 int model_ns(int kind) { return kind == 0 ? 4 : kind == 1 ? 5 : 12; }
+
+// the pair kernels' shared memory for W warps per tile (the largest form:
+// ADMM mode with the Newton solver's staging) fits the device's per-block limit
+bool warps_fit(const oca_scene *sc, int W) {
+    return pair_smem_bytes(sc->dim, dsize(sc->dtype), W, 1, 1, sc->FR, sc->FO) <= (size_t)sc->ctx->smem_optin;
+}
 
 oca_status check_model(const oca_scene *sc, const oca_model *m) {
     if (!m || m->kind < 0 || m->kind > 2) return OCA_ERR_INVALID_ARGUMENT;
@@ -258,6 +265,24 @@ oca_status scale_impl(oca_scene *sc, const oca_model *m, const void *states, voi
     a.verdict = verdict;
     a.status = status;
     OCA_CK(launch_scale<T>(a, sc->dim, sc->n_tiles, sc->W, st));
+    return OCA_OK;
+}
+
+template <typename T>
+oca_status cert_impl(oca_scene *sc, const oca_model *m, const void *states, const void *lambda, const void *mu,
+                     double *margin, cudaStream_t st) {
+    CertArgs<T> a;
+    a.meta = sc->d_meta;
+    a.tiles = sc->d_tiles;
+    a.g = make_geom<T>(sc);
+    a.model = make_model<double>(m);
+    a.states = static_cast<const T *>(states);
+    a.P = sc->P;
+    a.part_radius = sc->d_part_radius;
+    a.lambda = static_cast<const T *>(lambda);
+    a.mu = static_cast<const T *>(mu);
+    a.margin = margin;
+    OCA_CK(launch_cert<T>(a, sc->n_tiles, sc->W, st));
     return OCA_OK;
 }
 
@@ -895,7 +920,8 @@ oca_status oca_create(oca_ctx **out, int device) {
     oca_ctx *c = new (std::nothrow) oca_ctx;
     if (!c) return OCA_ERR_NO_MEMORY;
     c->device = device;
-    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
         delete c;
         return OCA_ERR_CUDA;
     }
@@ -1036,6 +1062,7 @@ oca_status oca_scene_create(oca_ctx *ctx, const oca_scene_desc *d, oca_scene **o
     std::nth_element(Ms.begin(), Ms.begin() + Ms.size() / 2, Ms.end());
     const int Mmed = Ms[Ms.size() / 2];
     sc->W = std::max(1, std::min(16, (Mmed + 7) / 8));
+    while (sc->W > 1 && !warps_fit(sc, sc->W)) --sc->W;
 
     const size_t ts = dsize(d->dtype);
     const int PK = d->dim + d->dim * d->dim;
@@ -1132,6 +1159,7 @@ oca_status oca_scene_info_get(const oca_scene *sc, oca_scene_info *info) {
 
 oca_status oca_scene_set_warps(oca_scene *sc, int warps) {
     if (!sc || warps < 1 || warps > 16) return OCA_ERR_INVALID_ARGUMENT;
+    if (!warps_fit(sc, warps)) return OCA_ERR_CAPACITY;
     sc->W = warps;
     return OCA_OK;
 }
@@ -1149,6 +1177,17 @@ oca_status oca_scale_detect_batch(oca_ctx *ctx, const oca_scene *scene, const oc
     if (sc->dtype == OCA_F32)
         return scale_impl<float>(sc, model, states, alpha, lambda, mu, margin, verdict, status, st);
     return scale_impl<double>(sc, model, states, alpha, lambda, mu, margin, verdict, status, st);
+}
+
+oca_status oca_cert_margin_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model, const void *states,
+                                 const void *lambda, const void *mu, double *margin, void *stream) {
+    if (!ctx || !scene || !states || !lambda || !mu || !margin) return OCA_ERR_INVALID_ARGUMENT;
+    oca_scene *sc = const_cast<oca_scene *>(scene);
+    oca_status e = check_model(sc, model);
+    if (e != OCA_OK) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (sc->dtype == OCA_F32) return cert_impl<float>(sc, model, states, lambda, mu, margin, st);
+    return cert_impl<double>(sc, model, states, lambda, mu, margin, st);
 }
 
 oca_status oca_pair_qp_batch(oca_ctx *ctx, const oca_scene *scene, const oca_model *model, const void *states,

@@ -186,6 +186,21 @@ struct ScaleArgs {
     int *status;    // [P] or null
 };
 
+// FP64 certificate margin of caller-given dual variables (oca_cert_margin_batch)
+template <typename T>
+struct CertArgs {
+    const ScenMeta *meta;
+    const Tile *tiles;
+    Geom<T> g;
+    DevModel<double> model;     // poses are formed in FP64 from the stored states
+    const T *states;            // [n_states][NS]
+    long long P;
+    const double *part_radius;  // [P_tot]
+    const T *lambda;            // [FR][P]
+    const T *mu;                // [FO][P]
+    double *margin;             // [P]
+};
+
 template <typename T>
 struct RicArgs {
     const ScenMeta *meta;

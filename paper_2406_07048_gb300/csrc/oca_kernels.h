@@ -11,8 +11,14 @@ cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pair(const PairArgs<T> &a, int dim, int mode, int solver, int n_tiles, int W, cudaStream_t st);
 
+// dynamic shared memory of a pair-kernel launch with W warps per tile
+size_t pair_smem_bytes(int dim, size_t es, int W, int mode, int solver, int FR, int FO);
+
 template <typename T>
 cudaError_t launch_scale(const ScaleArgs<T> &a, int dim, int n_tiles, int W, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_cert(const CertArgs<T> &a, int n_tiles, int W, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_riccati(const RicArgs<T> &a, bool f32, cudaStream_t st);

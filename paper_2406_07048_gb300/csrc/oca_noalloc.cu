@@ -3,8 +3,8 @@
 // oca_scale_detect_batch needs an oca_scene, whose creation allocates device
 // memory (metadata, work tiles, the pose buffer).  Some callers cannot
 // allocate at all: a real-time control loop that must not enter the CUDA
-// allocator (it can block or synchronise the device), code running inside a
-// stream capture or a host callback, or a plugin whose host forbids heap use.
+// allocator (it can block or synchronise the device), or a plugin whose host
+// forbids heap use.
 // oca_scale_detect_noalloc serves them: its scratch (the face counts and part
 // links copied from the host metadata, and the poses of the scenario's
 // (part, t) lanes) lives in the file-scope device array below, the scenario's

@@ -609,6 +609,82 @@ __global__ void __launch_bounds__(512) k_scale(ScaleArgs<T> a) {
 }
 
 // ============================================================================
+// FP64 weak-duality margin of given dual variables (Sec. III-B): for any
+// lambda, mu >= 0 and any (alpha, x) feasible for eqn:scale_opt,
+//   alpha b^T lambda >= r^T x - d'^T mu  with  r = A^T lambda + C'^T mu,
+// and |x| <= alpha D (x lies in alpha P, D = the part's largest vertex norm),
+// so alpha* >= -d'^T mu / (b^T lambda + |r| D).  The pose is formed in FP64
+// from the stored state, so the bound holds for the geometry as stored.
+// Same tile shape as k_scale: lanes over (part, t), warps over obstacles.
+// ============================================================================
+template <typename T, int KIND>
+__global__ void __launch_bounds__(512) k_cert(CertArgs<T> a) {
+    constexpr int D = MDims<KIND>::D, NS = MDims<KIND>::NS;
+    const Tile tile = a.tiles[blockIdx.x];
+    const ScenMeta sm = a.meta[tile.scen];
+    const int lane = threadIdx.x, warp = threadIdx.y, W = blockDim.y;
+    const int Q = sm.NP * sm.N;
+    const int q = tile.q0 + lane;
+    if (q >= Q) return;
+    const long long P = a.P;
+    const int FR = a.g.FR, FO = a.g.FO;
+    const int part = q / sm.N, t = q % sm.N + 1;
+    const int gp = sm.part0 + part;
+    double st[NS], off[D], rho[D], R[D * D];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) st[i] = double(a.states[(long long)(sm.state0 + t) * NS + i]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) off[i] = double(a.g.part_off[gp * D + i]);
+    part_pose<double, KIND>(a.model, a.g.part_link[gp], off, st, rho, R, nullptr, nullptr, nullptr);
+    const T *A = a.g.part_A + (long long)gp * FR * D;
+    const T *b = a.g.part_b + (long long)gp * FR;
+    const int nr = a.g.part_nf[gp];
+    const double Dr = a.part_radius[gp];
+    for (int j = warp; j < sm.M; j += W) {
+        const int gm = sm.obs0 + j;
+        const T *Cw = a.g.obs_C + (long long)gm * FO * D;
+        const T *dw = a.g.obs_d + (long long)gm * FO;
+        const int no = a.g.obs_nf[gm];
+        const long long p = sm.pair0 + (long long)j * Q + q;
+        bool ok = true;
+        double bl = 0.0, dm = 0.0, r[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) r[i] = 0.0;
+        for (int k = 0; k < nr; ++k) {
+            const double l = double(a.lambda[(long long)k * P + p]);
+            ok = ok && l >= 0.0 && isfinite(l);
+            bl += double(ldg(b + k)) * l;
+#pragma unroll
+            for (int i = 0; i < D; ++i) r[i] += double(ldg(A + k * D + i)) * l;
+        }
+        for (int m = 0; m < no; ++m) {
+            const double u = double(a.mu[(long long)m * P + p]);
+            ok = ok && u >= 0.0 && isfinite(u);
+            double c[D], cr = 0.0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                c[i] = double(ldg(Cw + m * D + i));
+                cr += c[i] * rho[i];
+            }
+            dm += (double(ldg(dw + m)) - cr) * u;
+            // body-frame normal C'_m = c_m^T R
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                double cb = 0.0;
+#pragma unroll
+                for (int l = 0; l < D; ++l) cb += c[l] * R[l * D + i];
+                r[i] += cb * u;
+            }
+        }
+        double rn = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) rn += r[i] * r[i];
+        const double den = bl + sqrt(rn) * Dr;
+        a.margin[p] = (ok && den > 0.0) ? -dm / den : -DBL_MAX;
+    }
+}
+
+// ============================================================================
 // launchers
 // ============================================================================
 template <typename T, int KIND>
@@ -629,12 +705,17 @@ cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+size_t pair_smem_bytes(int dim, size_t es, int W, int mode, int solver, int FR, int FO) {
+    const int nstat = dim * (dim + 1) / 2 + dim + dim * dim;
+    size_t b = 0;
+    if (solver == 1) b += (size_t)4 * FO * 32 * W * es + (size_t)W * (FR + FO + 2 + dim) * 32 * es;
+    if (mode == 1) b += (size_t)W * nstat * 32 * es + (size_t)W * 2 * sizeof(double);
+    return b;
+}
+
 template <typename T, int D>
 size_t pair_smem(int W, int mode, int solver, int FR, int FO) {
-    size_t b = 0;
-    if (solver == 1) b += (size_t)4 * FO * 32 * W * sizeof(T) + (size_t)W * (FR + FO + 2 + D) * 32 * sizeof(T);
-    if (mode == 1) b += (size_t)W * StatDims<D>::NSTAT * 32 * sizeof(T) + (size_t)W * 2 * sizeof(double);
-    return b;
+    return pair_smem_bytes(D, sizeof(T), W, mode, solver, FR, FO);
 }
 
 template <typename T, int D, int MODE, int SOLVER, int NR>
@@ -672,11 +753,26 @@ cudaError_t launch_scale(const ScaleArgs<T> &a, int dim, int n_tiles, int W, cud
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_cert(const CertArgs<T> &a, int n_tiles, int W, cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const dim3 blk(32, W);
+    switch (a.model.kind) {
+        case 0: k_cert<T, 0><<<n_tiles, blk, 0, st>>>(a); break;
+        case 1: k_cert<T, 1><<<n_tiles, blk, 0, st>>>(a); break;
+        case 2: k_cert<T, 2><<<n_tiles, blk, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_pose<float>(const PoseArgs<float> &, int, cudaStream_t);
 template cudaError_t launch_pose<double>(const PoseArgs<double> &, int, cudaStream_t);
 template cudaError_t launch_pair<float>(const PairArgs<float> &, int, int, int, int, int, cudaStream_t);
 template cudaError_t launch_pair<double>(const PairArgs<double> &, int, int, int, int, int, cudaStream_t);
 template cudaError_t launch_scale<float>(const ScaleArgs<float> &, int, int, int, cudaStream_t);
 template cudaError_t launch_scale<double>(const ScaleArgs<double> &, int, int, int, cudaStream_t);
+template cudaError_t launch_cert<float>(const CertArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_cert<double>(const CertArgs<double> &, int, int, cudaStream_t);
 
 }  // namespace oca

@@ -158,7 +158,13 @@ def test_autograd_function_matches_backward(B, ctx):
     d = ds.obs_d.clone().requires_grad_(True)
     shift = torch.zeros(sc.obs_d.shape[0], sc.dim, dtype=torch.float64, device=ds.device, requires_grad=True)
     cost = B.admm_cost(pb, d, shift, max_iter=K, **KW)
+    # another forward on the same problem (other offsets) and a plain solve of
+    # its scene between this forward and its backward change nothing: each
+    # forward solves on a scene of its own
+    other = B.admm_cost(pb, d.detach() + 0.05, shift.detach(), max_iter=K, **KW)
+    B.Problem(ds).solve(max_iter=3, **KW)
     gd, gs = torch.autograd.grad(cost.sum(), (d, shift))
+    assert torch.isfinite(other).all()
     g = _gpu_grads(B, ctx, sc, K, torch.float64)
     assert np.allclose(gd.cpu().numpy(), g["obs_offset"], rtol=1e-12, atol=1e-14)
     assert np.allclose(gs.cpu().numpy(), g["obs_center"], rtol=1e-12, atol=1e-14)

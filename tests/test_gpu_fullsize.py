@@ -135,3 +135,37 @@ def test_admm_fullsize_sampled_scenarios(big, ora, B):
         a, b = int(sc.state_begin[s]), int(sc.state_begin[s + 1])
         assert np.abs(s_g[a:b] - ref["s"][a:b]).max() < 2e-2
         assert float(rep["cost"][s]) == pytest.approx(ref["cost"][s], rel=1e-2)
+
+
+def test_autotune_warps_sets_the_fastest_and_restores_the_problem():
+    """DeviceScene.autotune_warps times short solves per candidate, sets the
+    fastest and leaves the problem's state as it found it."""
+    from paper_2406_07048_gb300 import _build, binding
+    _build.build()
+    sc = synth.config3(n_scen=64)
+    ctx = binding.Context(0)
+    ds = binding.DeviceScene(ctx, sc, torch.float32)
+    pb = binding.Problem(ds)
+    before = [t.clone() for t in (pb.s, pb.u, pb.y, pb.zeta, pb.xi)]
+    times = ds.autotune_warps(pb, candidates=(1, 2, 4), iters=4)
+    assert sorted(times) == [1, 2, 4] and all(v > 0 for v in times.values())
+    assert ds.warps == min(times, key=times.get)
+    for a, b in zip(before, (pb.s, pb.u, pb.y, pb.zeta, pb.xi)):
+        assert torch.equal(a, b)
+
+
+def test_set_warps_rejects_shared_memory_beyond_the_device_limit():
+    """Quadrotor scenes (20 obstacle faces, 3-D) need about 15 KB of pair-kernel
+    shared memory per warp: 16 warps per tile exceed the per-block limit and
+    are refused with OCA_ERR_CAPACITY before any launch; 4 are accepted."""
+    from paper_2406_07048_gb300 import _build, binding
+    _build.build()
+    sc = synth.config4(n_scen=1)
+    assert sc.fo_max == 20 and sc.fr_max == 6
+    ctx = binding.Context(0)
+    ds = binding.DeviceScene(ctx, sc, torch.float32)
+    with pytest.raises(binding.OcaError) as e:
+        ds.warps = 16
+    assert e.value.code == 5
+    ds.warps = 4
+    assert ds.warps == 4

@@ -418,3 +418,83 @@ def test_scene_validation_errors(B, ctx):
     h = C.c_void_p()
     assert B.lib().oca_scene_create(ctx.h, C.byref(d), C.byref(h)) == 1
     ds.close()
+
+
+def _as_stored(sc, dtype):
+    """The scene with its geometry rounded to the device precision, so that
+    the oracle sees the numbers the GPU holds."""
+    import dataclasses
+    if dtype == F64:
+        return sc
+    r = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    return dataclasses.replace(sc, obs_C=r(sc.obs_C), obs_d=r(sc.obs_d), part_A=r(sc.part_A), part_b=r(sc.part_b),
+                               part_off=r(sc.part_off))
+
+
+def _oracle_margins(ora, sc, states, lam, mu, pairs):
+    out = np.empty(len(pairs))
+    for i, p in enumerate(pairs):
+        Cb, db, A, b, nr, nf = _pose(ora, sc, states, int(p))
+        out[i] = ora.cert_margin(A, b, Cb, db, lam[p, :nr], mu[p, :nf])
+    return out
+
+
+@pytest.mark.parametrize("name,dtype", [("c1", F64), ("c2", F32), ("c3", F32), ("c4", F32), ("c4", F64)])
+def test_cert_margin_of_given_duals(B, ctx, ora, name, dtype):
+    """oca_cert_margin_batch (Sec. III-B weak duality) on certificates that
+    are NOT optimal, so that r = A^T lambda + C'^T mu != 0 and the part radius
+    matters: random nonnegative (lambda, mu), and the LP's optimal certificate
+    perturbed.  Element-wise against the oracle's FP64 margin on the same
+    stored inputs (relative 1e-12, floored at 1), and a valid lower bound of
+    the oracle's alpha* for every pair."""
+    sc = _as_stored(_scene(name), dtype)
+    rng = np.random.default_rng(17)
+    states = synth.random_states(sc, rng, 2.0, 0.5)
+    if dtype == F32:
+        states = states.astype(np.float32).astype(np.float64)
+    ds = B.DeviceScene(ctx, sc, dtype)
+    st_d = ds.tensor(states)
+    ref = ora.scale_batch(sc, states)
+    P = sc.n_pairs
+    lam_r = rng.exponential(1.0, (P, sc.fr_max)) * (rng.uniform(size=(P, sc.fr_max)) < 0.6)
+    mu_r = rng.exponential(1.0, (P, sc.fo_max)) * (rng.uniform(size=(P, sc.fo_max)) < 0.5)
+    lam_p = ref["lam"] + 1e-3 * rng.uniform(size=ref["lam"].shape)
+    mu_p = ref["mu"] + 1e-3 * rng.uniform(size=ref["mu"].shape)
+    for lam, mu in ((lam_r, mu_r), (lam_p, mu_p)):
+        if dtype == F32:
+            lam, mu = lam.astype(np.float32).astype(np.float64), mu.astype(np.float32).astype(np.float64)
+        m_g = B.cert_margin(ds, st_d, ds.to_device_pairs(lam), ds.to_device_pairs(mu)).cpu().numpy()
+        torch.cuda.synchronize()
+        sample = rng.choice(P, min(400, P), replace=False)
+        m_o = _oracle_margins(ora, sc, states, lam, mu, sample)
+        g = m_g[sample]
+        none = ~np.isfinite(m_o)                 # no bound (denominator 0): the GPU says -DBL_MAX
+        assert (g[none] < -1e300).all()
+        err = np.abs(g[~none] - m_o[~none]) / np.maximum(1.0, np.abs(m_o[~none]))
+        assert err.max() <= 1e-12, (err.max(), sample[~none][err.argmax()])
+        ok = m_g > -1e300
+        assert (m_g[ok] <= ref["alpha"][ok] + 1e-9 * np.maximum(1.0, ref["alpha"][ok])).all()
+
+
+def test_cert_margin_of_admm_duals(B, ctx, ora):
+    """The final check of an ADMM solve: the margin of its returned y at the
+    returned trajectory equals the oracle's on the same (FP64) numbers and
+    never exceeds the oracle's alpha* there."""
+    sc = synth.config2()
+    ds = B.DeviceScene(ctx, sc, F64)
+    pb = B.Problem(ds)
+    pb.solve(max_iter=40)
+    torch.cuda.synchronize()
+    FR, FO = sc.fr_max, sc.fo_max
+    m_g = B.cert_margin(ds, pb.s, pb.y[:FR], pb.y[FR:FR + FO]).cpu().numpy()
+    y = ds.to_host_pairs(pb.y)
+    s = pb.s.double().cpu().numpy()
+    rng = np.random.default_rng(3)
+    sample = rng.choice(sc.n_pairs, 500, replace=False)
+    m_o = _oracle_margins(ora, sc, s, y[:, :FR], y[:, FR:FR + FO], sample)
+    err = np.abs(m_g[sample] - m_o) / np.maximum(1.0, np.abs(m_o))
+    assert err.max() <= 1e-12
+    al = ora.scale_batch(sc, s)["alpha"]
+    assert (m_g <= al + 1e-9 * np.maximum(1.0, al)).all()
+    # the ADMM's multipliers are not the LP's optimum: r != 0 for most pairs
+    assert np.mean(m_g < al - 1e-6) > 0.5
