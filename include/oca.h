@@ -148,10 +148,11 @@ oca_status oca_scene_info_get(const oca_scene *scene, oca_scene_info *info);
  * DeviceScene.autotune_warps in the Python binding times the fused pair
  * kernel of short solves for each candidate and sets the fastest.
  * Errors: OCA_ERR_INVALID_ARGUMENT (warps outside 1..16), OCA_ERR_CAPACITY
- * (the pair kernels' shared memory for that many warps,
- * (5 fo_max + fr_max + dim + 2 + nstat) * 32 * warps elements plus 16 bytes per
- * warp with nstat = 9 in 2-D and 18 in 3-D, exceeds the device's per-block
- * limit). */
+ * (more than the 12 warps per tile the pair kernels are compiled for, or
+ * their shared memory for that many warps,
+ * ((4 + dim) fo_max + fr_max + fo_max + dim + 2 + nstat) * 32 * warps elements
+ * plus 2 (dim + 1) fo_max elements and 16 bytes per warp, nstat = 9 in 2-D and
+ * 18 in 3-D, exceeds the device's per-block limit). */
 oca_status oca_scene_set_warps(oca_scene *scene, int warps);
 int oca_scene_get_warps(const oca_scene *scene); /* -1 if scene == NULL */
 

@@ -97,6 +97,18 @@ OCA_HD inline double m_rsqrt(double x) {
     return 1.0 / sqrt(x);
 #endif
 }
+// 1 / x for a positive normal x: in FP32 on the device the hardware
+// approximation of the reciprocal (about 1 ulp; used for metric weights, where
+// any positive value gives a valid method and the solve uses the same value
+// throughout), otherwise the IEEE division
+OCA_HD inline float m_rcp(float x) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(1.0f, x);
+#else
+    return 1.0f / x;
+#endif
+}
+OCA_HD inline double m_rcp(double x) { return 1.0 / x; }
 OCA_HD inline float m_abs(float x) { return fabsf(x); }
 OCA_HD inline double m_abs(double x) { return fabs(x); }
 template <typename T> OCA_HD inline T m_eps();

@@ -60,8 +60,11 @@ __global__ void k_pose(PoseArgs<T> a) {
 #ifndef OCA_PAIR_MIN_BLOCKS
 #define OCA_PAIR_MIN_BLOCKS 1
 #endif
+// 384 threads (12 warps) at most per CTA lets the compiler keep the pair
+// kernel's state in registers (about 165 per thread) without spilling;
+// measured faster than the 128-register form of a 512-thread bound
 #ifndef OCA_PAIR_MAX_THREADS
-#define OCA_PAIR_MAX_THREADS 512
+#define OCA_PAIR_MAX_THREADS 384
 #endif
 template <typename T, int D, int MODE, int SOLVER, int NR>
 __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_pair(PairArgs<T> a) {
@@ -97,15 +100,25 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
     const int j0 = split ? 2 * warp + hh : warp, JS = split ? 2 * W : W;
     const long long P = a.P;
     const int FR = a.g.FR, FO = a.g.FO;
-    // shared memory: [staged face data 4 x FO x BT] [next obstacle's pair data W x NPF x 32]
-    // [statistics W x NSTAT x 32] [residuals W x 2 (double)]; the first two with SOLVER 1 only
+    // shared memory: [staged face data (4 + D) x FO x BT] [next obstacle's pair data
+    // W x NPF x 32] [next obstacle's halfspaces W x 2 x FO x (D + 1)] [statistics
+    // W x NSTAT x 32] [residuals W x 2 (double)]; the first three with SOLVER 1 only
     const int NY = FR + FO + 1, NPF = NY + 1 + D;  // y components, zeta, xi
+    const int NOB = FO * (D + 1);                  // one obstacle's C and d
     T *stg = reinterpret_cast<T *>(smem_raw);
-    T *pfb = stg + (SOLVER == 1 ? 4 * FO * BT : 0);
-    T *red = pfb + (SOLVER == 1 ? W * NPF * 32 : 0);
+    T *pfb = stg + (SOLVER == 1 ? (4 + D) * FO * BT : 0);
+    T *obb = pfb + (SOLVER == 1 ? W * NPF * 32 : 0);
+    T *red = obb + (SOLVER == 1 ? W * 2 * NOB : 0);
     // this lane's column of its warp's prefetch buffer: component c at pw[c * 32]
     // (lambda_k at k, mu_m at FR + m, gamma at FR + FO, zeta at NY, xi_i at NY + 1 + i)
     T *pw = pfb + warp * NPF * 32 + lane;
+    // the halfspaces of the obstacle this lane's (half-)warp works on: C [FO][D], d [FO]
+    T *ob = obb + (warp * 2 + hh) * NOB;
+    // the lanes sharing that buffer: the valid lanes of this warp (or half-warp);
+    // they copy it together and meet at __syncwarp(gmask) around each use
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const unsigned gmask = split ? (vmask & (hh ? 0xffff0000u : 0x0000ffffu)) : vmask;
+    const int g_n = __popc(gmask), g_r = __popc(gmask & ((1u << lane) - 1u));
 
     Lane<T, D> L;
     SsnLane<T, D, NR> SL;
@@ -129,10 +142,9 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
         L.b = a.g.part_b + (long long)gp * FR;
         L.nr = a.g.part_nf[gp];
         const T rho_p = a.prox;
+        const T irho = T(1) / rho_p;
         if constexpr (SOLVER == 1) {
             // robot-part constants of the proximal metric (registers)
-#pragma unroll
-            for (int i = 0; i < D * D; ++i) SL.R[i] = L.R[i];
             SL.nr = L.nr;
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
@@ -146,18 +158,20 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                 if (!(a2 > T(0))) a2 = T(1);
                 SL.b[k] = bk;
                 SL.iD[k] = T(1) / a2;
-                SL.iDr[k] = SL.iD[k] / rho_p;
                 SL.Db[k] = a2 / bk;
+                SL.iDr[k] = SL.iD[k] / rho_p;
                 SL.bD[k] = bk * SL.iD[k];
                 SL.b2D[k] = bk * SL.bD[k];
                 SL.rD[k] = rho_p * a2;
                 SL.yl[k] = T(0);
             }
             SL.BT = BT;
+            SL.FOBT = FO * BT;
             SL.sdp = stg + tid;
             SL.siD = stg + FO * BT + tid;
             SL.syb = stg + 2 * FO * BT + tid;
             SL.sq = stg + 3 * FO * BT + tid;
+            SL.scb = stg + 4 * FO * BT + tid;
         }
         // SOLVER 1: the pair data of this warp's next obstacle are copied to
         // shared memory asynchronously while the current obstacle is solved
@@ -174,6 +188,13 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                 cp_async_elem(pw + NY * 32, a.zeta + pn);
 #pragma unroll
                 for (int i = 0; i < D; ++i) cp_async_elem(pw + (NY + 1 + i) * 32, a.xi + (long long)i * P + pn);
+                // the obstacle's halfspaces, split over the lanes sharing them
+                const T *Cn = a.g.obs_C + (long long)gmn * FO * D;
+                const T *dn = a.g.obs_d + (long long)gmn * FO;
+                for (int e = g_r; e < non * (D + 1); e += g_n) {
+                    if (e < non * D) cp_async_elem(ob + e, Cn + e);
+                    else cp_async_elem(ob + FO * D + (e - non * D), dn + (e - non * D));
+                }
                 cp_async_commit();
             }
         };
@@ -194,12 +215,13 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                     for (int m = 0; m < L.no; ++m) y_out[(long long)(FR + m) * P + p] = y_in[(long long)(FR + m) * P + p];
                     y_out[(long long)(FR + FO) * P + p] = y_in[(long long)(FR + FO) * P + p];
                 }
-                prefetch(j + JS);
+                prefetch(j + JS);  // nothing was copied for this obstacle: the buffers are free
                 continue;
             }
             T zeta, xi[D];
             if constexpr (SOLVER == 1) {
-                cp_async_wait_all();  // this obstacle's copies (issued by this lane)
+                cp_async_wait_all();  // this obstacle's copies issued by this lane
+                __syncwarp(gmask);    // ... and by the other lanes sharing its halfspaces
                 zeta = pw[NY * 32];
 #pragma unroll
                 for (int i = 0; i < D; ++i) xi[i] = pw[(NY + 1 + i) * 32];
@@ -242,25 +264,34 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                     T c[D], cr = T(0), c2 = T(0);
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
-                        c[i] = ldg(L.C + m * D + i);
+                        c[i] = ob[m * D + i];
                         w0[i] += yv * c[i];
                         cr += c[i] * L.rho[i];
                         c2 += c[i] * c[i];
                     }
-                    const T dm = ldg(L.d + m);
+                    const T dm = ob[FO * D + m];
                     del0 += yv * dm;
                     const T dp = dm - cr;
                     const T Dm = dp * dp + c2;
-                    const T iDm = T(1) / (rho_p * Dm);
+                    const T iDm = m_rcp(rho_p * Dm);
                     const int o = m * BT + tid;
                     stg[o] = dp;
                     stg[FO * BT + o] = iDm;
                     stg[2 * FO * BT + o] = yv;
                     stg[3 * FO * BT + o] = rho_p * Dm * yv * yv;
+                    // body-frame normal c'_m = R^T c_m
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * c[k];
+                        stg[(4 + i) * FO * BT + o] = acc;
+                    }
                 }
                 SL.ybg = pw[(FR + FO) * 32];
                 del0 += SL.ybg;
-                prefetch(j + JS);  // the buffer is free again
+                __syncwarp(gmask);  // every sharing lane has read the halfspaces
+                prefetch(j + JS);   // the buffers are free again
             } else {
                 for (int g = 0; g < ng; ++g) {
                     const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
@@ -376,9 +407,8 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                     ws[1 + i] = acc;
                 }
                 SL.no = L.no;
-                SL.C = L.C;
-                SsnEval<T, D, NR> est;
-                status = ssn_solve_staged<T, D, NR>(SL, rho_p, bq, ws, est);
+                SsnKeep<T, NR> est;
+                status = ssn_solve_staged<T, D, NR>(SL, rho_p, irho, bq, ws, est);
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     if (k < L.nr) {
@@ -390,46 +420,45 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                         for (int i = 0; i < D; ++i) a1[i] += yv * SL.a[k][i];
                     }
                 }
-                T Rw[D];
+                // mu from the staged body-frame data; the sums sd = sum mu d',
+                // sc = sum mu c' give K^T y, and w1 = R sc, del1 = sd + rho.w1 + gamma
+                // the world-frame sums of the statistics
+                T sd = T(0), sc[D];
 #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int k = 0; k < D; ++k) acc += L.R[i * D + k] * ws[1 + k];
-                    Rw[i] = acc;
-                }
+                for (int i = 0; i < D; ++i) sc[i] = T(0);
                 for (int m = 0; m < L.no; ++m) {
                     const int o = m * BT + tid;
                     const T dp = stg[o], iDm = stg[FO * BT + o], ybm = stg[2 * FO * BT + o];
                     T c[D], cw = T(0);
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
-                        c[i] = ldg(L.C + m * D + i);
-                        cw += c[i] * Rw[i];
+                        c[i] = stg[(4 + i) * FO * BT + o];
+                        cw += c[i] * ws[1 + i];
                     }
                     const T yv = fmax(T(0), ybm - (ws[0] * dp + cw) * iDm);
                     const T dlt = yv - ybm;
                     dy2 += dlt * dlt;
                     yo[(long long)(FR + m) * P] = yv;
+                    sd += yv * dp;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) w1[i] += yv * c[i];
-                    del1 += yv * ldg(L.d + m);
+                    for (int i = 0; i < D; ++i) sc[i] += yv * c[i];
                 }
-                const T gv = fmax(T(0), SL.ybg - ws[0] / rho_p);
+                const T gv = fmax(T(0), SL.ybg - ws[0] * irho);
                 yo[(long long)(FR + FO) * P] = gv;
-                del1 += gv;
                 // v = K^T y + bq from the written y
+                v[0] = bq[0] + sd + gv;
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[1 + i] = bq[1 + i] + a1[i] + sc[i];
                 T wr1 = T(0);
 #pragma unroll
-                for (int i = 0; i < D; ++i) wr1 += w1[i] * L.rho[i];
-                v[0] = bq[0] + del1 - wr1;
-#pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    T acc = bq[1 + i] + a1[i];
+                    T acc = T(0);
 #pragma unroll
-                    for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * w1[k];
-                    v[1 + i] = acc;
+                    for (int k = 0; k < D; ++k) acc += L.R[i * D + k] * sc[k];
+                    w1[i] = acc;
+                    wr1 += acc * L.rho[i];
                 }
+                del1 = sd + wr1 + gv;
             }
             if (MODE == 0) {
                 if (a.v_out) {
@@ -705,10 +734,14 @@ cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+int pair_max_warps() { return OCA_PAIR_MAX_THREADS / 32; }
+
 size_t pair_smem_bytes(int dim, size_t es, int W, int mode, int solver, int FR, int FO) {
     const int nstat = dim * (dim + 1) / 2 + dim + dim * dim;
     size_t b = 0;
-    if (solver == 1) b += (size_t)4 * FO * 32 * W * es + (size_t)W * (FR + FO + 2 + dim) * 32 * es;
+    if (solver == 1)
+        b += (size_t)(4 + dim) * FO * 32 * W * es + (size_t)W * (FR + FO + 2 + dim) * 32 * es +
+             (size_t)W * 2 * FO * (dim + 1) * es;
     if (mode == 1) b += (size_t)W * nstat * 32 * es + (size_t)W * 2 * sizeof(double);
     return b;
 }

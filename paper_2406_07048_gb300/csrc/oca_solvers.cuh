@@ -854,8 +854,6 @@ OCA_HD inline T ssn_value(const Lane<T, D> &L, const T *ybar, long long P, int F
 // ============================================================================
 template <typename T, int D, int NR>
 struct SsnLane {
-    // pose
-    T R[D * D];
     // robot part
     int nr;
     T a[NR][D], b[NR];
@@ -866,11 +864,12 @@ struct SsnLane {
     T rD[NR];    // rho |a_k|^2
     T iD[NR];    // 1 / |a_k|^2
     T yl[NR];    // previous lambda
-    // obstacle faces (shared memory) and world normals (global)
+    // obstacle faces, staged per lane in shared memory at [m * BT] (+ tid):
+    // body-frame offset d'_m, 1 / (rho |K_m|^2), previous mu_m, rho |K_m|^2 mu_m^2,
+    // and the body-frame normal c'_m = R^T c_m (component i at scb + i * FO * BT)
     int no;
-    const T *C;          // [no][D] world normals
-    const T *sdp, *siD, *syb, *sq;  // [m * BT] + tid
-    int BT;
+    const T *sdp, *siD, *syb, *sq, *scb;
+    int BT, FOBT;
     // slack
     T ybg;
 };
@@ -884,7 +883,7 @@ struct SsnEval {
 };
 
 template <typename T, int D, int NR>
-OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, const T bq[D + 1], const T w[D + 1],
+OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, const T bq[D + 1], const T w[D + 1],
                                    SsnEval<T, D, NR> &st) {
     constexpr int V = D + 1;
     // lambda: z_k = ybar_k - a_k.w1 / (rho |a_k|^2), breakpoints t_k = z_k |a_k|^2 / b_k
@@ -959,68 +958,61 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
             }
         }
     }
-    // faces: h_m = w0 d'_m + c_m.(R w1), mu_m = max(0, ybar_m - h_m / (rho |K_m|^2))
-    T Rw[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc += L.R[i * D + k] * w[1 + k];
-        Rw[i] = acc;
-    }
-    // M' = sum_active [d'; c][d'; c]^T / |K_m|^2 (lifted with diag(1, R^T) afterwards)
+    // faces: h_m = w0 d'_m + c'_m.w1 (body frame), mu_m = max(0, ybar_m - h_m / (rho |K_m|^2))
+    // M = sum_active [d'; c'][d'; c']^T / |K_m|^2
     T Mp[V][V];
 #pragma unroll
     for (int i = 0; i < V; ++i)
 #pragma unroll
         for (int j = 0; j < V; ++j) Mp[i][j] = T(0);
+    // proximal terms of the faces, doubled: rho |K|^2 (mu - ybar)^2; an
+    // inactive face (mu_m = 0) contributes its constant rho |K|^2 ybar^2 only
+    T face_pen = T(0);
     for (int m = 0; m < L.no; ++m) {
         const int o = m * L.BT;
         const T dp = L.sdp[o], iDm = L.siD[o], yb = L.syb[o];
         T c[D], cw = T(0);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            c[i] = ldg(L.C + m * D + i);
-            cw += c[i] * Rw[i];
+            c[i] = L.scb[i * L.FOBT + o];
+            cw += c[i] * w[1 + i];
         }
         const T hm = w[0] * dp + cw;
-        const T mu = fmax(T(0), yb - hm * iDm);
+        const T mu = yb - hm * iDm;
         if (mu > T(0)) {
-            half_pen += T(0.5) * hm * hm * iDm;   // 0.5 rho |K|^2 (mu - ybar)^2 with mu - ybar = -h iD
-            const T wgt = rho_p * iDm;             // 1 / |K_m|^2
+            face_pen += hm * hm * iDm;     // mu - ybar = -h iD
+            const T wgt = rho_p * iDm;     // 1 / |K_m|^2
             T e[V];
             e[0] = dp;
 #pragma unroll
             for (int i = 0; i < D; ++i) e[1 + i] = c[i];
+            T we[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) we[i] = wgt * e[i];
 #pragma unroll
             for (int i = 0; i < V; ++i)
 #pragma unroll
-                for (int j = 0; j <= i; ++j) Mp[i][j] += wgt * e[i] * e[j];
-        } else {
-            half_pen += T(0.5) * L.sq[o];          // 0.5 rho |K|^2 ybar^2
-        }
-        lin += hm * mu;
-        lmag += (m_abs(w[0] * dp) + m_abs(cw)) * mu;
-        sd += mu * dp;
+                for (int j = 0; j <= i; ++j) Mp[i][j] += we[i] * e[j];
+            lin += hm * mu;
+            sd += mu * dp;
 #pragma unroll
-        for (int i = 0; i < D; ++i) sc[i] += mu * c[i];
-        mag += mu * (m_abs(dp) + T(1));
+            for (int i = 0; i < D; ++i) sc[i] += mu * c[i];
+            lmag += (m_abs(w[0] * dp) + m_abs(cw)) * mu;
+            mag += mu * (m_abs(dp) + T(1));
+        } else {
+            face_pen += L.sq[o];
+        }
     }
-    const T gam = fmax(T(0), L.ybg - w[0] / rho_p);
+    half_pen += T(0.5) * face_pen;
+    const T gam = fmax(T(0), L.ybg - w[0] * irho);
     {
         const T dg = gam - L.ybg;
         half_pen += T(0.5) * rho_p * dg * dg;
     }
     lin += w[0] * gam;
-    mag += gam;
     st.Kty[0] = sd + gam;
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        T acc = a1[i];
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * sc[k];
-        st.Kty[1 + i] = acc;
-    }
+    for (int i = 0; i < D; ++i) st.Kty[1 + i] = a1[i] + sc[i];
     T ww = T(0), bw = T(0);
 #pragma unroll
     for (int i = 0; i < V; ++i) {
@@ -1028,44 +1020,40 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
         bw += bq[i] * w[i];
     }
     st.psi = T(0.5) * ww - bw - (half_pen + lin);
-    st.mag = mag;
+    st.mag = mag + gam;
     st.pmag = T(0.5) * ww + m_abs(bw) + half_pen + lmag + m_abs(w[0] * gam);
-    // H = rho I + diag(1, R^T) M' diag(1, R) + e0 e0^T [gamma active] + lambda part
+    // H = rho I + M + e0 e0^T [gamma active] + lambda part
+    const T ibb = bb > T(0) ? T(1) / bb : T(0);
 #pragma unroll
     for (int i = 0; i < V; ++i)
 #pragma unroll
-        for (int j = i + 1; j < V; ++j) Mp[i][j] = Mp[j][i];
-    st.H[0][0] = rho_p + Mp[0][0] + (gam > T(0) ? T(1) : T(0));
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * Mp[1 + k][0];
-        st.H[1 + i][0] = st.H[0][1 + i] = acc;
-    }
-    const T ibb = bb > T(0) ? T(1) / bb : T(0);
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            T acc = (i == j) ? rho_p : T(0);
-#pragma unroll
-            for (int k = 0; k < D; ++k)
-#pragma unroll
-                for (int l = 0; l < D; ++l) acc += L.R[k * D + i] * Mp[1 + k][1 + l] * L.R[l * D + j];
-            st.H[1 + i][1 + j] = acc + Ha[i][j] - ba[i] * ba[j] * ibb;
+        for (int j = 0; j <= i; ++j) {
+            T hv = Mp[i][j] + (i == j ? rho_p : T(0));
+            if (i == 0 && j == 0 && gam > T(0)) hv += T(1);
+            if (i > 0 && j > 0) hv += Ha[i - 1][j - 1] - ba[i - 1] * ba[j - 1] * ibb;
+            st.H[i][j] = hv;
+            st.H[j][i] = hv;
         }
 }
 
+// The part of an evaluation the solve carries from one pass to the next:
+// the accepted point's lambda (the result), psi and its rounding scale.
+template <typename T, int NR>
+struct SsnKeep {
+    T lam[NR];
+    T psi, pmag;
+};
+
 template <typename T, int D, int NR>
-OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T bq[D + 1], T w[D + 1],
-                                   SsnEval<T, D, NR> &st) {
+OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, const T bq[D + 1], T w[D + 1],
+                                   SsnKeep<T, NR> &st) {
     // One loop with a single evaluation site: every pass evaluates y(w) at
     // one point -- the start point, or a trial w + t d of the line search --
     // and then either backtracks, or accepts the trial and computes the next
-    // Newton direction.  (The same sequence of evaluations as a Newton loop
-    // with a nested line search; but the large evaluation code exists once,
-    // and lanes of a warp in different phases share evaluation passes.)
+    // Newton direction from that evaluation.  (The same sequence of
+    // evaluations as a Newton loop with a nested line search; but the large
+    // evaluation code exists once, and lanes of a warp in different phases
+    // share evaluation passes.)
     constexpr int V = D + 1;
     int status = OCA_PAIR_ITER_CAP;
     T dlt[V], wt[V], tstep = T(1), gd = T(0);
@@ -1075,7 +1063,8 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
 #pragma unroll
         for (int i = 0; i < V; ++i) wt[i] = started ? w[i] + tstep * dlt[i] : w[i];
         SsnEval<T, D, NR> trial;
-        ssn_eval_staged<T, D, NR>(L, rho_p, bq, wt, trial);
+        ssn_eval_staged<T, D, NR>(L, rho_p, irho, bq, wt, trial);
+        bool stop = false;
         if (started) {
             const bool ok = trial.psi <= st.psi + T(1e-4) * tstep * gd + T(8) * m_eps<T>() * (st.pmag + trial.pmag);
             if (!ok && ls < 29) {
@@ -1088,23 +1077,27 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
                 ++ls;
                 continue;
             }
-#pragma unroll
-            for (int i = 0; i < V; ++i) w[i] = wt[i];
-            st = trial;
             if (!ok) {
                 status = OCA_PAIR_OK;  // no decrease at rounding level
-                break;
+                stop = true;
             }
-            if (++it >= 60) break;
+            if (++it >= 60) stop = true;
         } else {
-            st = trial;
             started = true;
         }
+        // accept the trial
+#pragma unroll
+        for (int i = 0; i < V; ++i) w[i] = wt[i];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) st.lam[k] = trial.lam[k];
+        st.psi = trial.psi;
+        st.pmag = trial.pmag;
+        if (stop) break;
         // convergence test and the next Newton direction at w
-        T F[V], fn = T(0), scale = T(1) + st.mag;
+        T F[V], fn = T(0), scale = T(1) + trial.mag;
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            F[i] = w[i] - bq[i] - st.Kty[i];
+            F[i] = w[i] - bq[i] - trial.Kty[i];
             fn = fmax(fn, m_abs(F[i]));
             scale = fmax(scale, fmax(m_abs(w[i]), m_abs(bq[i])));
         }
@@ -1116,14 +1109,9 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, const T 
             status = OCA_PAIR_NONFINITE;
             break;
         }
-        T G[V][V];
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            dlt[i] = -rho_p * F[i];
-#pragma unroll
-            for (int j = 0; j < V; ++j) G[i][j] = st.H[i][j];
-        }
-        if (!chol_solve<T, V>(G, dlt, V, T(0))) {
+        for (int i = 0; i < V; ++i) dlt[i] = -rho_p * F[i];
+        if (!chol_solve<T, V>(trial.H, dlt, V, T(0))) {
 #pragma unroll
             for (int i = 0; i < V; ++i) dlt[i] = -F[i];
         }
