@@ -92,7 +92,9 @@ def test_pair_qp_fullsize(big, ora, B, warps):
     assert err[ok].max() <= 1e-4, (name, err[ok].max())
     y_g = out["y"][:, torch.as_tensor(idx, device=ds.device)].double().cpu().numpy().T
     yerr = np.abs(y_g - ref["y"]).max(axis=1) / np.maximum(1.0, np.abs(ref["y"]).max(axis=1))
-    assert yerr[ok].max() <= 5e-3, (name, yerr[ok].max())
+    print(f"[fullsize pair qp {name}] obj rel err max {err[ok].max():.3g}, y rel err max {yerr[ok].max():.3g} "
+          f"median {np.median(yerr[ok]):.3g}")
+    assert yerr[ok].max() <= 2e-4, (name, yerr[ok].max())   # measured <= 2e-6
 
 
 def test_admm_fullsize_sampled_scenarios(big, ora, B):
@@ -133,8 +135,11 @@ def test_admm_fullsize_sampled_scenarios(big, ora, B):
         assert st[s] == 0, (name, s, st[s], its[s], ref["iters"][s])
         assert abs(int(its[s]) - int(ref["iters"][s])) <= max(3, 0.1 * ref["iters"][s])
         a, b = int(sc.state_begin[s]), int(sc.state_begin[s + 1])
-        assert np.abs(s_g[a:b] - ref["s"][a:b]).max() < 2e-2
-        assert float(rep["cost"][s]) == pytest.approx(ref["cost"][s], rel=1e-2)
+        print(f"[fullsize {name} scen {s}] max |s_gpu - s_oracle| {np.abs(s_g[a:b] - ref['s'][a:b]).max():.3g}")
+        # measured: 1e-5 (2-D), 8e-4 (quadrotor, 12 states over N = 40)
+        assert np.abs(s_g[a:b] - ref["s"][a:b]).max() < 3e-3
+        print(f"[fullsize {name} scen {s}] cost rel {abs(float(rep['cost'][s]) / ref['cost'][s] - 1):.3g}")
+        assert float(rep["cost"][s]) == pytest.approx(ref["cost"][s], rel=1e-3)
 
 
 def test_autotune_warps_sets_the_fastest_and_restores_the_problem():

@@ -3,7 +3,12 @@ same seeded inputs.  Tolerances: FP32 alpha* and the pair-QP objective within
 1e-4 relative, identical collision verdicts where |alpha* - 1| > 1e-3; FP64
 runs within 1e-9.  Where several results are correct (y* of the pair QP with
 prox = 0) the unique quantities (v*, objective) are compared and the GPU's y
-is checked for feasibility and optimality."""
+is checked for feasibility and optimality.
+
+"Relative" errors here are floored at 1: |x_gpu - x_oracle| / max(1, |x_oracle|),
+so for quantities below 1 in magnitude (most pair objectives, alpha* of
+overlapping pairs) the bound is absolute.  The tests print the measured
+errors (pytest -s)."""
 import numpy as np
 import pytest
 import torch
@@ -142,6 +147,11 @@ def test_pair_qp_prox0_parity(B, ctx, ora, name, dtype, warm):
     assert err.max() <= tol, (err.max(), int(err.argmax()), o_g[err.argmax()], o_o[err.argmax()], st[err.argmax()])
     v_g = ds.to_host_pairs(out["v"])
     verr = np.abs(v_g - ref["v"]).max(axis=1) / np.maximum(1.0, np.abs(ref["v"]).max(axis=1))
+    print(f"[prox0 {name} {dtype} warm={warm}] obj rel err max {err.max():.3g}, v rel err max {verr.max():.3g} "
+          f"median {np.median(verr):.3g}")
+    # prox = 0 is the paper's QP as printed: v* is unique but, where nearly
+    # parallel generators of distant obstacles meet, FP32 rounding moves it by
+    # up to ~4e-3 (measured) while the objective stays within 1e-4
     assert verr.max() <= (1e-7 if dtype == F64 else 5e-3), (verr.max(), int(verr.argmax()))
     assert (st != 3).all() and (st == 0).mean() > 0.99
     yg = ds.to_host_pairs(out["y"])
@@ -179,7 +189,10 @@ def test_pair_qp_prox_parity(B, ctx, ora, name, dtype, prox):
     assert err[ok].max() <= (1e-9 if dtype == F64 else 1e-4), (err[ok].max(), int(np.argmax(err * ok)))
     yg = ds.to_host_pairs(out["y"])
     yerr = np.abs(yg - ref["y"]).max(axis=1) / np.maximum(1.0, np.abs(ref["y"]).max(axis=1))
-    assert yerr[ok].max() <= (1e-7 if dtype == F64 else 5e-3), (yerr[ok].max(), int(np.argmax(yerr * ok)))
+    print(f"[prox {name} {dtype} {prox}] obj rel err max {err[ok].max():.3g}, y rel err max {yerr[ok].max():.3g} "
+          f"median {np.median(yerr[ok]):.3g}, capped {(~ok).sum()}")
+    # measured FP32 maxima 1e-6 .. 3e-5 on these scenes
+    assert yerr[ok].max() <= (1e-7 if dtype == F64 else 2e-4), (yerr[ok].max(), int(np.argmax(yerr * ok)))
 
 
 def test_pair_qp_in_place(B, ctx, ora):
@@ -260,8 +273,11 @@ def test_admm_fp32_matches_oracle(B, ctx, ora, name):
         assert abs(int(its[s]) - int(ref["iters"][s])) <= max(3, 0.1 * ref["iters"][s])
         a, b = int(sc.state_begin[s]), int(sc.state_begin[s + 1])
         ds_ = np.abs(pb.s.cpu().numpy()[a:b] - ref["s"][a:b]).max()
-        assert ds_ < 2e-2, (s, ds_)
-        assert float(rep["cost"][s]) == pytest.approx(ref["cost"][s], rel=1e-2)
+        print(f"[admm fp32 {name} scen {s}] iters gpu {int(its[s])} oracle {int(ref['iters'][s])}, "
+              f"max |s_gpu - s_oracle| {ds_:.3g}, cost rel {abs(float(rep['cost'][s]) / ref['cost'][s] - 1):.3g}")
+        # measured: trajectories within 2.4e-5, costs within 6e-6 relative
+        assert ds_ < 1e-3, (s, ds_)
+        assert float(rep["cost"][s]) == pytest.approx(ref["cost"][s], rel=1e-4)
     # collision verdicts of the final plans (GPU scale detection on the GPU plan,
     # oracle LP on the oracle plan)
     sd = B.scale_detect(ds, pb.s)
@@ -303,7 +319,13 @@ def test_edge_cases(B, ctx, ora):
         pb = B.Problem(ds)
         rep = pb.solve(max_iter=50)
         rr = ora.admm_batch(sc, max_iter=50)
-        assert int(rep["iters"][0]) == rr["iters"][0] or dtype == F32
+        it_g, it_o = int(rep["iters"][0]), int(rr["iters"][0])
+        print(f"[edge {dtype}] iters gpu {it_g} oracle {it_o}")
+        if dtype == F64:
+            assert it_g == it_o
+        else:
+            # FP32 pair QPs: the stopping test may trigger a few iterations apart
+            assert abs(it_g - it_o) <= max(3, it_o // 10), (it_g, it_o)
 
 
 def _padding_mask(sc):
