@@ -423,6 +423,8 @@ def gpu_arm(args):
         out["precision_form"] = precision_form(ctx)
     if rank == 0 and not args.no_lemke:
         out["pair_solver_comparison"] = solver_comparison(ds, wl.s0, wl.y0, params)
+    if rank == 0 and args.lq:
+        out["lq_scan_vs_sequential"] = lq_crossover(ctx)
     if rank == 0 and args.closed_loop > 0:
         out["closed_loop"] = closed_loop(ctx, args, params, world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -540,6 +542,55 @@ def precision_form(ctx):
                 "QP at the final iterate (prox as the solve)"}
     ds.close()
     return out
+
+
+def lq_crossover(ctx, grid=((12, 4, (16, 64, 256, 1024), (1, 4, 16, 64, 256)),
+                               (5, 2, (16, 64, 256, 1024), (1, 16, 256)))):
+    """The step-2 LQ problem solved by the sequential Riccati recursion and in
+    parallel-in-time form (oca_lq_solve), on random problems of the models'
+    sizes (12 states / 4 inputs: quadrotor; 5 / 2: tractor-trailer): device
+    time of one batched solve (CUDA events, mean of 10 after 2 warm-ups)."""
+    import torch
+
+    from paper_2406_07048_gb300 import binding
+    rows = []
+    rng = np.random.default_rng(0)
+    for ns, nu, Ns, Ss in grid:
+        for N in Ns:
+            for S in Ss:
+                A = torch.eye(ns, dtype=torch.float64, device="cuda").expand(S, N, ns, ns) + \
+                    0.05 * torch.randn(S, N, ns, ns, dtype=torch.float64, device="cuda")
+                Bm = 0.2 * torch.randn(S, N, ns, nu, dtype=torch.float64, device="cuda")
+                c = 0.1 * torch.randn(S, N, ns, dtype=torch.float64, device="cuda")
+                L = torch.randn(S, N + 1, ns, ns, dtype=torch.float64, device="cuda")
+                Q = L @ L.transpose(-1, -2) / ns + 0.1 * torch.eye(ns, dtype=torch.float64, device="cuda")
+                q = torch.randn(S, N + 1, ns, dtype=torch.float64, device="cuda")
+                Lr = torch.randn(S, N, nu, nu, dtype=torch.float64, device="cuda")
+                R = Lr @ Lr.transpose(-1, -2) / nu + 0.1 * torch.eye(nu, dtype=torch.float64, device="cuda")
+                r = torch.randn(S, N, nu, dtype=torch.float64, device="cuda")
+                s0 = torch.randn(S, ns, dtype=torch.float64, device="cuda")
+                work = torch.empty(binding.lq_workspace_bytes(ns, nu, N, S), dtype=torch.uint8, device="cuda")
+                row = {"ns": ns, "nu": nu, "N": N, "S": S}
+                outs = {}
+                for name, method in (("sequential_ms", binding.OCA_LQ_SEQUENTIAL), ("scan_ms", binding.OCA_LQ_SCAN)):
+                    for _ in range(2):
+                        o = binding.lq_solve(ctx, A, Bm, c, Q, q, R, r, s0, method=method, want_value=False, work=work)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(10):
+                        o = binding.lq_solve(ctx, A, Bm, c, Q, q, R, r, s0, method=method, want_value=False, work=work)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    row[name] = e0.elapsed_time(e1) / 10
+                    outs[name] = o
+                d = (outs["scan_ms"]["s"] - outs["sequential_ms"]["s"]).abs().max().item()
+                row["max_state_diff"] = d
+                row["scan_speedup"] = row["sequential_ms"] / row["scan_ms"]
+                rows.append(row)
+    return {"what": "step-2 LQ problem, FP64, random dense stage matrices: sequential Riccati recursion "
+                    "(one CTA per problem) vs parallel-in-time composition (log2(N+1) rounds), "
+                    "device time per batched solve incl. gains and rollout",
+            "rows": rows}
 
 
 def solver_comparison(ds, s0, y_cold, params):
@@ -745,6 +796,7 @@ def main():
     ap.add_argument("--quad", type=int, default=64, help="scenes of the quadrotor line (0: off)")
     ap.add_argument("--quad-steps", type=int, default=3, help="timed steps of the quadrotor line")
     ap.add_argument("--precision", type=int, default=1, help="precision-form line (config 2 vs the oracle; 0: off)")
+    ap.add_argument("--lq", type=int, default=1, help="sequential vs parallel-in-time LQ solve line (0: off)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -418,6 +418,46 @@ oca_status oca_scale_detect_noalloc(const oca_scene_desc *desc, const oca_model 
                                     void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* The step-2 LQ problem, batched, sequential or parallel in time            */
+/* ------------------------------------------------------------------------ */
+/* Step 2 of the ADMM (Sec. IV-B eqn:ADMM_state_updates, solved as one QP per
+ * iteration) is an LQ problem of the form
+ *   min  sum_{t=0..N} 0.5 s_t^T Q_t s_t + q_t^T s_t + sum_{t<N} 0.5 u_t^T R_t u_t + r_t^T u_t
+ *   s.t. s_{t+1} = A_t s_t + B_t u_t + c_t,  s_0 given,
+ * with Q_t positive semidefinite and R_t positive definite.  oca_lq_solve
+ * solves a batch of S independent such problems (same ns, nu, N) in FP64:
+ *   OCA_LQ_SEQUENTIAL  the backward Riccati recursion over t, one CTA per problem;
+ *   OCA_LQ_SCAN        parallel in time: the stage relations of the optimality
+ *                      conditions (state and costate, s_{t+1} = A s + b - C lam_{t+1},
+ *                      lam_t = J s - eta + A^T lam_{t+1}) composed associatively in
+ *                      ceil(log2(N + 1)) rounds, one CTA per composition, giving
+ *                      every stage's value function at once; it trades about
+ *                      log2(N) times the recursion's arithmetic for a dependent
+ *                      chain of log2(N) rounds instead of N steps (for long
+ *                      horizons with few problems).
+ * Both then form the gains K_t, k_t of every stage in parallel and roll the
+ * closed loop out from s_0 (one warp per problem).
+ * Layouts (device, row-major, problem-major):
+ *   A [S][N][ns][ns], B [S][N][ns][nu], c [S][N][ns], Q [S][N+1][ns][ns],
+ *   q [S][N+1][ns], R [S][N][nu][nu], r [S][N][nu], s0 [S][ns];
+ *   out: s [S][N+1][ns], u [S][N][nu], P [S][N+1][ns][ns] and p [S][N+1][ns]
+ *   (value functions V_t(s) = 0.5 s^T P_t s + p_t^T s + const, each may be NULL),
+ *   status [S] int32 (0 solved; 1 a singular R_t, R_t + B^T P B or elimination
+ *   pivot, or a non-finite value: that problem's outputs are meaningless).
+ * work: caller-owned device workspace, 256-byte aligned, at least
+ * oca_lq_workspace_bytes(...) bytes; nothing is allocated.  ns <= 12, nu <= 4,
+ * N <= OCA_MAX_LQ_HORIZON, S <= 65535 (else OCA_ERR_CAPACITY).
+ * Errors: OCA_ERR_INVALID_ARGUMENT, OCA_ERR_CAPACITY, OCA_ERR_CUDA. */
+#define OCA_LQ_SEQUENTIAL 0
+#define OCA_LQ_SCAN 1
+#define OCA_MAX_LQ_HORIZON 65535
+oca_status oca_lq_workspace_bytes(int32_t ns, int32_t nu, int32_t N, int32_t n_problems, int64_t *bytes);
+oca_status oca_lq_solve(oca_ctx *ctx, int32_t method, int32_t ns, int32_t nu, int32_t N, int32_t n_problems,
+                        const double *A, const double *B, const double *c, const double *Q, const double *q,
+                        const double *R, const double *r, const double *s0, double *s, double *u, double *P,
+                        double *p, int32_t *status, void *work, int64_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Kernel timing                                                            */
 /* ------------------------------------------------------------------------ */
 typedef struct {

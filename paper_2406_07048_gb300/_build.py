@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liboca.so")
 SOURCES = ["oca_api.cu", "oca_pair.cu", "oca_riccati.cu", "oca_adjoint.cu", "oca_mpc.cu", "oca_lemke.cu", "oca_noalloc.cu",
-           "oca_peak.cu"]
+           "oca_peak.cu", "oca_scan.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC, "--expt-relaxed-constexpr"]

@@ -77,7 +77,7 @@ EXPORTED = ["oca_create", "oca_destroy", "oca_status_string", "oca_scene_create"
             "oca_pair_qp_batch", "oca_admm_solve", "oca_profile_enable", "oca_profile_read",
             "oca_scale_detect_noalloc", "oca_admm_tape_bytes", "oca_admm_solve_taped", "oca_admm_backward",
             "oca_mpc_run", "oca_pair_qp_lemke_batch", "oca_admm_fixed_point_tape_bytes", "oca_fp64_peak",
-            "oca_cert_margin_batch"]
+            "oca_cert_margin_batch", "oca_lq_workspace_bytes", "oca_lq_solve"]
 
 
 def lib():
@@ -108,6 +108,10 @@ def lib():
         L.oca_scale_detect_batch.restype = I
         L.oca_cert_margin_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, P, P]
         L.oca_cert_margin_batch.restype = I
+        L.oca_lq_workspace_bytes.argtypes = [I, I, I, I, C.POINTER(C.c_int64)]
+        L.oca_lq_workspace_bytes.restype = I
+        L.oca_lq_solve.argtypes = [P, I, I, I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, C.c_int64, P]
+        L.oca_lq_solve.restype = I
         L.oca_pair_qp_batch.argtypes = [P, P, C.POINTER(ModelC), P, P, P, D, P, P, P, P, P, P]
         L.oca_pair_qp_batch.restype = I
         L.oca_admm_solve.argtypes = [P, P, C.POINTER(ModelC), C.POINTER(AdmmParams), P, P, P, P, P, P,
@@ -355,6 +359,43 @@ def cert_margin(ds: DeviceScene, states: torch.Tensor, lam: torch.Tensor, mu: to
     _check(lib().oca_cert_margin_batch(ds.ctx.h, ds.h, C.byref(ds.model), _ptr(states), _ptr(lam.contiguous()),
                                        _ptr(mu.contiguous()), _ptr(margin), _stream(stream)), "oca_cert_margin_batch")
     return margin
+
+
+OCA_LQ_SEQUENTIAL, OCA_LQ_SCAN = 0, 1
+
+
+def lq_workspace_bytes(ns: int, nu: int, N: int, n_problems: int) -> int:
+    """oca_lq_workspace_bytes."""
+    n = C.c_int64(0)
+    _check(lib().oca_lq_workspace_bytes(int(ns), int(nu), int(N), int(n_problems), C.byref(n)),
+           "oca_lq_workspace_bytes")
+    return int(n.value)
+
+
+def lq_solve(ctx: Context, A, B, c, Q, q, R, r, s0, method: int = OCA_LQ_SCAN, want_value=True, work=None,
+             stream=None):
+    """oca_lq_solve on FP64 device tensors shaped [S][N][..] (A, B, c, R, r),
+    [S][N+1][..] (Q, q), [S][ns] (s0): returns s, u, P, p and status."""
+    S, N1, ns = Q.shape[0], Q.shape[1], Q.shape[2]
+    N = N1 - 1
+    nu = R.shape[-1] if R is not None and R.dim() == 4 else 1
+    dev = Q.device
+    f64 = lambda t: None if t is None else t.to(torch.float64).contiguous()
+    A, B, c, Q, q, R, r, s0 = map(f64, (A, B, c, Q, q, R, r, s0))
+    s = torch.empty(S, N + 1, ns, dtype=torch.float64, device=dev)
+    u = torch.empty(S, max(N, 0), nu, dtype=torch.float64, device=dev)
+    P = torch.empty(S, N + 1, ns, ns, dtype=torch.float64, device=dev) if want_value else None
+    p = torch.empty(S, N + 1, ns, dtype=torch.float64, device=dev) if want_value else None
+    status = torch.empty(S, dtype=torch.int32, device=dev)
+    wb = lq_workspace_bytes(ns, nu, N, S)
+    if work is None:
+        work = torch.empty(wb, dtype=torch.uint8, device=dev)
+    _check(lib().oca_lq_solve(ctx.h, int(method), int(ns), int(nu), int(N), int(S), _ptr(A) if N > 0 else None,
+                              _ptr(B) if N > 0 else None, _ptr(c) if N > 0 else None, _ptr(Q), _ptr(q),
+                              _ptr(R) if N > 0 else None, _ptr(r) if N > 0 else None, _ptr(s0), _ptr(s),
+                              _ptr(u) if N > 0 else None, _ptr(P), _ptr(p), _ptr(status), _ptr(work),
+                              C.c_int64(work.numel()), _stream(stream)), "oca_lq_solve")
+    return dict(s=s, u=u, P=P, p=p, status=status)
 
 
 def scale_detect_noalloc(ds: DeviceScene, states: torch.Tensor, want_certificate: bool = True, stream=None):
