@@ -100,13 +100,16 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
     const int j0 = split ? 2 * warp + hh : warp, JS = split ? 2 * W : W;
     const long long P = a.P;
     const int FR = a.g.FR, FO = a.g.FO;
-    // shared memory: [staged face data (4 + D) x FO x BT] [next obstacle's pair data
+    // shared memory: [staged face records, BT lanes x LS] [next obstacle's pair data
     // W x NPF x 32] [next obstacle's halfspaces W x 2 x FO x (D + 1)] [statistics
     // W x NSTAT x 32] [residuals W x 2 (double)]; the first three with SOLVER 1 only
     const int NY = FR + FO + 1, NPF = NY + 1 + D;  // y components, zeta, xi
     const int NOB = FO * (D + 1);                  // one obstacle's C and d
     T *stg = reinterpret_cast<T *>(smem_raw);
-    T *pfb = stg + (SOLVER == 1 ? (4 + D) * FO * BT : 0);
+    // per-lane staged face records (FaceRec), lane stride LS
+    const int LS = face_lane_stride<T, D>(FO);
+    T *pfb = stg + (SOLVER == 1 ? LS * BT : 0);
+    T *lrec = stg + tid * LS;
     T *obb = pfb + (SOLVER == 1 ? W * NPF * 32 : 0);
     T *red = obb + (SOLVER == 1 ? W * 2 * NOB : 0);
     // this lane's column of its warp's prefetch buffer: component c at pw[c * 32]
@@ -165,13 +168,7 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                 SL.rD[k] = rho_p * a2;
                 SL.yl[k] = T(0);
             }
-            SL.BT = BT;
-            SL.FOBT = FO * BT;
-            SL.sdp = stg + tid;
-            SL.siD = stg + FO * BT + tid;
-            SL.syb = stg + 2 * FO * BT + tid;
-            SL.sq = stg + 3 * FO * BT + tid;
-            SL.scb = stg + 4 * FO * BT + tid;
+            SL.sl = lrec;
         }
         // SOLVER 1: the pair data of this warp's next obstacle are copied to
         // shared memory asynchronously while the current obstacle is solved
@@ -274,19 +271,16 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
                     const T dp = dm - cr;
                     const T Dm = dp * dp + c2;
                     const T iDm = m_rcp(rho_p * Dm);
-                    const int o = m * BT + tid;
-                    stg[o] = dp;
-                    stg[FO * BT + o] = iDm;
-                    stg[2 * FO * BT + o] = yv;
-                    stg[3 * FO * BT + o] = rho_p * Dm * yv * yv;
                     // body-frame normal c'_m = R^T c_m
+                    T cb[D];
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
                         T acc = T(0);
 #pragma unroll
                         for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * c[k];
-                        stg[(4 + i) * FO * BT + o] = acc;
+                        cb[i] = acc;
                     }
+                    face_store<T, D>(lrec + m * FaceRec<D>::N, dp, iDm, yv, rho_p * Dm * yv * yv, cb);
                 }
                 SL.ybg = pw[(FR + FO) * 32];
                 del0 += SL.ybg;
@@ -427,14 +421,10 @@ __global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_p
 #pragma unroll
                 for (int i = 0; i < D; ++i) sc[i] = T(0);
                 for (int m = 0; m < L.no; ++m) {
-                    const int o = m * BT + tid;
-                    const T dp = stg[o], iDm = stg[FO * BT + o], ybm = stg[2 * FO * BT + o];
-                    T c[D], cw = T(0);
+                    T dp, iDm, ybm, sqm, c[D], cw = T(0);
+                    face_load<T, D>(lrec + m * FaceRec<D>::N, dp, iDm, ybm, sqm, c);
 #pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        c[i] = stg[(4 + i) * FO * BT + o];
-                        cw += c[i] * ws[1 + i];
-                    }
+                    for (int i = 0; i < D; ++i) cw += c[i] * ws[1 + i];
                     const T yv = fmax(T(0), ybm - (ws[0] * dp + cw) * iDm);
                     const T dlt = yv - ybm;
                     dy2 += dlt * dlt;
@@ -739,9 +729,11 @@ int pair_max_warps() { return OCA_PAIR_MAX_THREADS / 32; }
 size_t pair_smem_bytes(int dim, size_t es, int W, int mode, int solver, int FR, int FO) {
     const int nstat = dim * (dim + 1) / 2 + dim + dim * dim;
     size_t b = 0;
-    if (solver == 1)
-        b += (size_t)(4 + dim) * FO * 32 * W * es + (size_t)W * (FR + FO + 2 + dim) * 32 * es +
-             (size_t)W * 2 * FO * (dim + 1) * es;
+    if (solver == 1) {
+        const size_t ls = dim == 2 ? (es == 4 ? face_lane_stride<float, 2>(FO) : face_lane_stride<double, 2>(FO))
+                                   : (es == 4 ? face_lane_stride<float, 3>(FO) : face_lane_stride<double, 3>(FO));
+        b += ls * 32 * W * es + (size_t)W * (FR + FO + 2 + dim) * 32 * es + (size_t)W * 2 * FO * (dim + 1) * es;
+    }
     if (mode == 1) b += (size_t)W * nstat * 32 * es + (size_t)W * 2 * sizeof(double);
     return b;
 }

@@ -864,15 +864,74 @@ struct SsnLane {
     T rD[NR];    // rho |a_k|^2
     T iD[NR];    // 1 / |a_k|^2
     T yl[NR];    // previous lambda
-    // obstacle faces, staged per lane in shared memory at [m * BT] (+ tid):
-    // body-frame offset d'_m, 1 / (rho |K_m|^2), previous mu_m, rho |K_m|^2 mu_m^2,
-    // and the body-frame normal c'_m = R^T c_m (component i at scb + i * FO * BT)
+    // obstacle faces, staged per lane in shared memory: record m at sl[m * kFaceRec]
+    // holds d'_m, 1 / (rho |K_m|^2), the previous mu_m, rho |K_m|^2 mu_m^2 and the
+    // body-frame normal c'_m = R^T c_m (FaceRec below)
     int no;
-    const T *sdp, *siD, *syb, *sq, *scb;
-    int BT, FOBT;
+    const T *sl;
     // slack
     T ybg;
 };
+
+// One staged obstacle face of one lane: [d', 1/(rho |K|^2), mu^k, rho |K|^2 (mu^k)^2,
+// c'_0 .. c'_{D-1}], padded to an even length so that a lane's records can be
+// read as 8-byte pairs.  A lane's records are contiguous; lanes are
+// face_lane_stride elements apart, an odd number of 8-byte units, so that
+// the lanes of a half-warp reading the same field hit distinct banks.
+template <int D>
+struct FaceRec {
+    static constexpr int N = (4 + D + 1) & ~1;
+};
+template <typename T, int D>
+OCA_HD inline int face_lane_stride(int FO) {
+    return FaceRec<D>::N * FO + (sizeof(T) == 4 ? 2 : 1);
+}
+template <typename T, int D>
+OCA_HD inline void face_load(const T *r, T &dp, T &iD, T &yb, T &sq, T (&c)[D]) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        const float2 a = *reinterpret_cast<const float2 *>(r);
+        const float2 b = *reinterpret_cast<const float2 *>(r + 2);
+        const float2 e = *reinterpret_cast<const float2 *>(r + 4);
+        dp = a.x;
+        iD = a.y;
+        yb = b.x;
+        sq = b.y;
+        c[0] = e.x;
+        c[1] = e.y;
+        if constexpr (D == 3) c[2] = r[6];
+        return;
+    }
+#endif
+    dp = r[0];
+    iD = r[1];
+    yb = r[2];
+    sq = r[3];
+#pragma unroll
+    for (int i = 0; i < D; ++i) c[i] = r[4 + i];
+}
+template <typename T, int D>
+OCA_HD inline void face_store(T *r, T dp, T iD, T yb, T sq, const T (&c)[D]) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float2 *>(r) = make_float2(dp, iD);
+        *reinterpret_cast<float2 *>(r + 2) = make_float2(yb, sq);
+        if constexpr (D == 2) {
+            *reinterpret_cast<float2 *>(r + 4) = make_float2(c[0], c[1]);
+        } else {
+            *reinterpret_cast<float2 *>(r + 4) = make_float2(c[0], c[1]);
+            r[6] = c[2];
+        }
+        return;
+    }
+#endif
+    r[0] = dp;
+    r[1] = iD;
+    r[2] = yb;
+    r[3] = sq;
+#pragma unroll
+    for (int i = 0; i < D; ++i) r[4 + i] = c[i];
+}
 
 template <typename T, int D, int NR>
 struct SsnEval {
@@ -969,14 +1028,10 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
     // inactive face (mu_m = 0) contributes its constant rho |K|^2 ybar^2 only
     T face_pen = T(0);
     for (int m = 0; m < L.no; ++m) {
-        const int o = m * L.BT;
-        const T dp = L.sdp[o], iDm = L.siD[o], yb = L.syb[o];
-        T c[D], cw = T(0);
+        T dp, iDm, yb, sqm, c[D], cw = T(0);
+        face_load<T, D>(L.sl + m * FaceRec<D>::N, dp, iDm, yb, sqm, c);
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            c[i] = L.scb[i * L.FOBT + o];
-            cw += c[i] * w[1 + i];
-        }
+        for (int i = 0; i < D; ++i) cw += c[i] * w[1 + i];
         const T hm = w[0] * dp + cw;
         const T mu = yb - hm * iDm;
         if (mu > T(0)) {
@@ -1000,7 +1055,7 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
             lmag += (m_abs(w[0] * dp) + m_abs(cw)) * mu;
             mag += mu * (m_abs(dp) + T(1));
         } else {
-            face_pen += L.sq[o];
+            face_pen += sqm;
         }
     }
     half_pen += T(0.5) * face_pen;
