@@ -943,7 +943,9 @@ struct SsnEval {
 
 template <typename T, int D, int NR>
 OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, const T bq[D + 1], const T w[D + 1],
-                                   SsnEval<T, D, NR> &st) {
+                                   int &amask, SsnEval<T, D, NR> &st) {
+    // amask: in, the robot faces active at the previous evaluation (or at the
+    // warm start); out, those active at w
     constexpr int V = D + 1;
     // lambda: z_k = ybar_k - a_k.w1 / (rho |a_k|^2), breakpoints t_k = z_k |a_k|^2 / b_k
     T z[NR], t[NR], h[NR];
@@ -956,30 +958,50 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
         z[k] = L.yl[k] - hk * L.iDr[k];
         t[k] = k < L.nr ? z[k] * L.Db[k] : T(-3.0e38);
     }
-    // threshold tau: on the active set {t_j >= tau}, sum b z - tau sum b^2/D = 1;
-    // the active set is the largest {t_j >= t_k} whose tau stays below t_k
-    // (s2 > 0, so tau_k < t_k is tested as s1 - 1 < t_k s2; one division at the end)
-    T bs1 = T(1), bs2 = T(1);
-    int best_n = -1;
+    // threshold tau: on the active set {t_j > tau}, sum b z - tau sum b^2/D = 1.
+    // The previous active set is tried first: it is the answer when its tau
+    // separates it from the other breakpoints (t_k > tau exactly on the set).
+    // Otherwise the full search: the active set is the largest {t_j >= t_k}
+    // whose tau stays below t_k (s2 > 0, so tau_k < t_k is tested as
+    // s1 - 1 < t_k s2).  One division either way.
+    T bs1 = T(0), bs2 = T(0);
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        T s1 = T(0), s2 = T(0);
-        int n = 0;
+    for (int k = 0; k < NR; ++k)
+        if (k < L.nr && ((amask >> k) & 1)) {
+            bs1 += L.b[k] * z[k];
+            bs2 += L.b2D[k];
+        }
+    bool hit = bs2 > T(0);
+    T inv = T(1) / (hit ? bs2 : T(1));
+    T tau = (bs1 - T(1)) * inv;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            if (j < L.nr && t[j] >= t[k]) {
-                s1 += L.b[j] * z[j];
-                s2 += L.b2D[j];
-                ++n;
+    for (int k = 0; k < NR; ++k)
+        if (k < L.nr) hit = hit && ((((amask >> k) & 1) != 0) == (t[k] > tau));
+    if (!hit) {
+        bs1 = T(1);
+        bs2 = T(1);
+        int best_n = -1;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            T s1 = T(0), s2 = T(0);
+            int n = 0;
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                if (j < L.nr && t[j] >= t[k]) {
+                    s1 += L.b[j] * z[j];
+                    s2 += L.b2D[j];
+                    ++n;
+                }
+            }
+            if (k < L.nr && s1 - T(1) < t[k] * s2 && n > best_n) {
+                best_n = n;
+                bs1 = s1;
+                bs2 = s2;
             }
         }
-        if (k < L.nr && s1 - T(1) < t[k] * s2 && n > best_n) {
-            best_n = n;
-            bs1 = s1;
-            bs2 = s2;
-        }
+        inv = T(1) / bs2;
+        tau = (bs1 - T(1)) * inv;  // 0 when no candidate qualified
     }
-    const T tau = (bs1 - T(1)) / bs2;  // 0 when no candidate qualified
     T half_pen = T(0), lin = T(0), lmag = T(0), mag = T(0);
     T a1[D], sc[D], sd = T(0);
 #pragma unroll
@@ -995,9 +1017,11 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
         for (int j = 0; j < D; ++j) Ha[i][j] = T(0);
     }
 #pragma unroll
+    int nmask = 0;
     for (int k = 0; k < NR; ++k) {
         const T lk = k < L.nr ? fmax(T(0), z[k] - tau * L.bD[k]) : T(0);
         st.lam[k] = lk;
+        nmask |= (lk > T(0) ? 1 : 0) << k;
         if (k < L.nr) {
             const T dl = lk - L.yl[k];
             half_pen += T(0.5) * L.rD[k] * dl * dl;
@@ -1078,7 +1102,9 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
     st.mag = mag + gam;
     st.pmag = T(0.5) * ww + m_abs(bw) + half_pen + lmag + m_abs(w[0] * gam);
     // H = rho I + M + e0 e0^T [gamma active] + lambda part
-    const T ibb = bb > T(0) ? T(1) / bb : T(0);
+    amask = nmask;
+    // 1 / sum_active b^2/D: the threshold's denominator when the sets agree
+    const T ibb = bb > T(0) ? (bb == bs2 ? inv : T(1) / bb) : T(0);
 #pragma unroll
     for (int i = 0; i < V; ++i)
 #pragma unroll
@@ -1114,11 +1140,15 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
     T dlt[V], wt[V], tstep = T(1), gd = T(0);
     bool started = false;
     int it = 0, ls = 0;
+    // robot faces active at the last evaluation; first guess: the warm start's
+    int amask = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) amask |= (k < L.nr && L.yl[k] > T(0) ? 1 : 0) << k;
     for (int pass = 0; pass < 1 + 60 * 30; ++pass) {
 #pragma unroll
         for (int i = 0; i < V; ++i) wt[i] = started ? w[i] + tstep * dlt[i] : w[i];
         SsnEval<T, D, NR> trial;
-        ssn_eval_staged<T, D, NR>(L, rho_p, irho, bq, wt, trial);
+        ssn_eval_staged<T, D, NR>(L, rho_p, irho, bq, wt, amask, trial);
         bool stop = false;
         if (started) {
             const bool ok = trial.psi <= st.psi + T(1e-4) * tstep * gd + T(8) * m_eps<T>() * (st.pmag + trial.pmag);
