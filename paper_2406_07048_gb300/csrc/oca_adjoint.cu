@@ -250,11 +250,12 @@ __global__ void __launch_bounds__(32) k_adj_traj(AdjTrajArgs<T> a) {
         a.sb[k2] = T(0);
     }
     __syncwarp();
-    F ru_diag[NU];
-#pragma unroll
-    for (int i = 0; i < NU; ++i)
+    // diagonal of Ru in shared memory, as in the forward kernel
+    __shared__ F ru_diag[NU];
+    for (int i = lane; i < NU; i += 32)
         ru_diag[i] = F(2) * F(a.model.Qu[i]) + F(a.damp) +
                      (bounded(a.model.u_lo[i], a.model.u_hi[i]) ? F(a.rho_box) : F(0));
+    __syncwarp();
     ric_factor<F, NS, NU>(scr, N, ru_diag);
     __shared__ F sc[NS];
     for (int i = lane; i < NS; i += 32) {
