@@ -60,14 +60,23 @@ __global__ void k_pose(PoseArgs<T> a) {
 #ifndef OCA_PAIR_MIN_BLOCKS
 #define OCA_PAIR_MIN_BLOCKS 1
 #endif
-// 384 threads (12 warps) at most per CTA lets the compiler keep the pair
-// kernel's state in registers (about 165 per thread) without spilling;
-// measured faster than the 128-register form of a 512-thread bound
-#ifndef OCA_PAIR_MAX_THREADS
-#define OCA_PAIR_MAX_THREADS 384
+// Launch bound of the pair kernel per dimension: 384 threads (12 warps) at
+// most per CTA in 2-D lets the compiler keep the kernel's state in about 165
+// registers per thread without spilling (measured faster than the
+// 128-register form of a 512-thread bound); the 3-D kernel (4 x 4 Newton
+// systems, up to 8 robot faces) needs about 245 and is bounded at 256 threads.
+#ifndef OCA_PAIR_MAX_THREADS_2D
+#define OCA_PAIR_MAX_THREADS_2D 384
 #endif
+#ifndef OCA_PAIR_MAX_THREADS_3D
+#define OCA_PAIR_MAX_THREADS_3D 256
+#endif
+template <int D>
+struct PairBound {
+    static constexpr int threads = D == 2 ? OCA_PAIR_MAX_THREADS_2D : OCA_PAIR_MAX_THREADS_3D;
+};
 template <typename T, int D, int MODE, int SOLVER, int NR>
-__global__ void __launch_bounds__(OCA_PAIR_MAX_THREADS, OCA_PAIR_MIN_BLOCKS) k_pair(PairArgs<T> a) {
+__global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_pair(PairArgs<T> a) {
     constexpr int V = D + 1, SM = D + 2, NSTAT = StatDims<D>::NSTAT, NW = StatDims<D>::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Tile tile = a.tiles[blockIdx.x];
@@ -724,7 +733,7 @@ cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-int pair_max_warps() { return OCA_PAIR_MAX_THREADS / 32; }
+int pair_max_warps(int dim) { return (dim == 2 ? PairBound<2>::threads : PairBound<3>::threads) / 32; }
 
 size_t pair_smem_bytes(int dim, size_t es, int W, int mode, int solver, int FR, int FO) {
     const int nstat = dim * (dim + 1) / 2 + dim + dim * dim;
