@@ -148,11 +148,13 @@ oca_status oca_scene_info_get(const oca_scene *scene, oca_scene_info *info);
  * DeviceScene.autotune_warps in the Python binding times the fused pair
  * kernel of short solves for each candidate and sets the fastest.
  * Errors: OCA_ERR_INVALID_ARGUMENT (warps outside 1..16), OCA_ERR_CAPACITY
- * (more than the 12 warps per tile the pair kernels are compiled for, or
- * their shared memory for that many warps,
- * ((4 + dim) fo_max + fr_max + fo_max + dim + 2 + nstat) * 32 * warps elements
- * plus 2 (dim + 1) fo_max elements and 16 bytes per warp, nstat = 9 in 2-D and
- * 18 in 3-D, exceeds the device's per-block limit). */
+ * (more warps per tile than the pair kernels are compiled for -- 16 for
+ * FP32 2-D scenes, 12 for FP64 2-D, 8 for 3-D -- or their shared memory for
+ * that many warps exceeds the device's per-block limit: per warp,
+ * (ls + fr_max + fo_max + dim + 2 + nstat) * 32 + 4 nob elements and 16
+ * bytes, with ls = 4 (fo_max | 1) in FP32 and 4 fo_max + 2 in FP64,
+ * nob = fo_max (nc + 1) rounded up to a multiple of 4, nc = 2 in 2-D and 4
+ * in 3-D, nstat = 9 in 2-D and 18 in 3-D). */
 oca_status oca_scene_set_warps(oca_scene *scene, int warps);
 int oca_scene_get_warps(const oca_scene *scene); /* -1 if scene == NULL */
 

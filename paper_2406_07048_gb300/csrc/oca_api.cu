@@ -102,7 +102,7 @@ int model_ns(int kind) { return kind == 0 ? 4 : kind == 1 ? 5 : 12; }
 // the pair kernels' shared memory for W warps per tile (the largest form:
 // ADMM mode with the Newton solver's staging) fits the device's per-block limit
 bool warps_fit(const oca_scene *sc, int W) {
-    return W <= pair_max_warps(sc->dim) &&
+    return W <= pair_max_warps(sc->dim, dsize(sc->dtype)) &&
            pair_smem_bytes(sc->dim, dsize(sc->dtype), W, 1, 1, sc->FR, sc->FO) <= (size_t)sc->ctx->smem_optin;
 }
 

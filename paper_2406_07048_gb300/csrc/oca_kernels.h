@@ -12,7 +12,7 @@ template <typename T>
 cudaError_t launch_pair(const PairArgs<T> &a, int dim, int mode, int solver, int n_tiles, int W, cudaStream_t st);
 
 // largest warps per tile the pair kernels are compiled for (their launch bound)
-int pair_max_warps(int dim);
+int pair_max_warps(int dim, size_t es);
 // dynamic shared memory of a pair-kernel launch with W warps per tile
 size_t pair_smem_bytes(int dim, size_t es, int W, int mode, int solver, int FR, int FO);
 

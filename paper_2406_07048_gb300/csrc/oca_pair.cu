@@ -60,23 +60,27 @@ __global__ void k_pose(PoseArgs<T> a) {
 #ifndef OCA_PAIR_MIN_BLOCKS
 #define OCA_PAIR_MIN_BLOCKS 1
 #endif
-// Launch bound of the pair kernel per dimension: 384 threads (12 warps) at
-// most per CTA in 2-D lets the compiler keep the kernel's state in about 165
-// registers per thread without spilling (measured faster than the
-// 128-register form of a 512-thread bound); the 3-D kernel (4 x 4 Newton
-// systems, up to 8 robot faces) needs about 245 and is bounded at 256 threads.
+// Launch bound of the pair kernel: 512 threads (16 warps) at most per CTA
+// for the FP32 2-D kernel, whose state fits 128 registers per thread without
+// spilling (16 resident warps per SM); 384 for the FP64 2-D kernel (about 165
+// registers); the 3-D kernel (4 x 4 Newton systems, up to 8 robot faces)
+// needs about 245 and is bounded at 256 threads.
 #ifndef OCA_PAIR_MAX_THREADS_2D
-#define OCA_PAIR_MAX_THREADS_2D 384
+#define OCA_PAIR_MAX_THREADS_2D 512
+#endif
+#ifndef OCA_PAIR_MAX_THREADS_2D_F64
+#define OCA_PAIR_MAX_THREADS_2D_F64 384
 #endif
 #ifndef OCA_PAIR_MAX_THREADS_3D
 #define OCA_PAIR_MAX_THREADS_3D 256
 #endif
-template <int D>
+template <typename T, int D>
 struct PairBound {
-    static constexpr int threads = D == 2 ? OCA_PAIR_MAX_THREADS_2D : OCA_PAIR_MAX_THREADS_3D;
+    static constexpr int threads =
+        D == 3 ? OCA_PAIR_MAX_THREADS_3D : (sizeof(T) == 4 ? OCA_PAIR_MAX_THREADS_2D : OCA_PAIR_MAX_THREADS_2D_F64);
 };
 template <typename T, int D, int MODE, int SOLVER, int NR>
-__global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_pair(PairArgs<T> a) {
+__global__ void __launch_bounds__(PairBound<T, D>::threads, OCA_PAIR_MIN_BLOCKS) k_pair(PairArgs<T> a) {
     constexpr int V = D + 1, SM = D + 2, NSTAT = StatDims<D>::NSTAT, NW = StatDims<D>::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Tile tile = a.tiles[blockIdx.x];
@@ -110,22 +114,25 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
     const long long P = a.P;
     const int FR = a.g.FR, FO = a.g.FO;
     // shared memory: [staged face records, BT lanes x LS] [next obstacle's pair data
-    // W x NPF x 32] [next obstacle's halfspaces W x 2 x FO x (D + 1)] [statistics
-    // W x NSTAT x 32] [residuals W x 2 (double)]; the first three with SOLVER 1 only
+    // W x NPF x 32] [halfspaces of the current and the next obstacle W x 2 x 2 x NOB]
+    // [statistics W x NSTAT x 32] [residuals W x 2 (double)]; the first three with
+    // SOLVER 1 only
+    constexpr int NC = NrmStride<D>::N;
     const int NY = FR + FO + 1, NPF = NY + 1 + D;  // y components, zeta, xi
-    const int NOB = FO * (D + 1);                  // one obstacle's C and d
+    const int NOB = obs_buf_elems<D>(FO);          // one obstacle's normals [FO][NC] and offsets [FO]
     T *stg = reinterpret_cast<T *>(smem_raw);
-    // per-lane staged face records (FaceRec), lane stride LS
-    const int LS = face_lane_stride<T, D>(FO);
+    // per-lane staged face records [d', iD, s, ybar], lane stride LS
+    const int LS = face_lane_stride<T>(FO);
     T *pfb = stg + (SOLVER == 1 ? LS * BT : 0);
     T *lrec = stg + tid * LS;
     T *obb = pfb + (SOLVER == 1 ? W * NPF * 32 : 0);
-    T *red = obb + (SOLVER == 1 ? W * 2 * NOB : 0);
+    T *red = obb + (SOLVER == 1 ? W * 4 * NOB : 0);
     // this lane's column of its warp's prefetch buffer: component c at pw[c * 32]
     // (lambda_k at k, mu_m at FR + m, gamma at FR + FO, zeta at NY, xi_i at NY + 1 + i)
     T *pw = pfb + warp * NPF * 32 + lane;
-    // the halfspaces of the obstacle this lane's (half-)warp works on: C [FO][D], d [FO]
-    T *ob = obb + (warp * 2 + hh) * NOB;
+    // the two halfspace buffers of this lane's (half-)warp: obstacle number c of
+    // its sweep (c = 0, 1, ...) uses buffer c & 1
+    T *ob2 = obb + (warp * 2 + hh) * 2 * NOB;
     // the lanes sharing that buffer: the valid lanes of this warp (or half-warp);
     // they copy it together and meet at __syncwarp(gmask) around each use
     const unsigned vmask = __ballot_sync(0xffffffffu, valid);
@@ -134,13 +141,13 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
 
     Lane<T, D> L;
     SsnLane<T, D, NR> SL;
-    T st_W[NW], st_Wc[D], st_E[D * D];
+    // this lane's Gauss-Newton statistics, accumulated in its own slots of the
+    // reduction buffer (W [NW], Wc [D], E [D*D] at rsl[k * 32])
+    T *rsl = red + warp * NSTAT * 32 + lane;
+    if (MODE == 1) {
 #pragma unroll
-    for (int k = 0; k < NW; ++k) st_W[k] = T(0);
-#pragma unroll
-    for (int k = 0; k < D; ++k) st_Wc[k] = T(0);
-#pragma unroll
-    for (int k = 0; k < D * D; ++k) st_E[k] = T(0);
+        for (int k = 0; k < NSTAT; ++k) rsl[k * 32] = T(0);
+    }
     double rp = 0.0, rd = 0.0;
 
     if (valid) {
@@ -156,32 +163,39 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
         const T rho_p = a.prox;
         const T irho = T(1) / rho_p;
         if constexpr (SOLVER == 1) {
-            // robot-part constants of the proximal metric (registers)
+            // robot-part constants of the lambda subproblem in its breakpoint
+            // form (registers): ta_k = R a_k / (prox b_k), w_k = b_k^2 / n_k,
+            // bD_k = b_k / n_k with n_k = |a_k|^2
             SL.nr = L.nr;
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                T a2 = T(0);
+                T a2 = T(0), ak[D];
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    SL.a[k][i] = k < L.nr ? ldg(L.A + k * D + i) : T(0);
-                    a2 += SL.a[k][i] * SL.a[k][i];
+                    ak[i] = k < L.nr ? ldg(L.A + k * D + i) : T(0);
+                    a2 += ak[i] * ak[i];
                 }
                 const T bk = k < L.nr ? ldg(L.b + k) : T(1);
                 if (!(a2 > T(0))) a2 = T(1);
-                SL.b[k] = bk;
-                SL.iD[k] = T(1) / a2;
-                SL.Db[k] = a2 / bk;
-                SL.iDr[k] = SL.iD[k] / rho_p;
-                SL.bD[k] = bk * SL.iD[k];
-                SL.b2D[k] = bk * SL.bD[k];
-                SL.rD[k] = rho_p * a2;
-                SL.yl[k] = T(0);
+                const T s = T(1) / (rho_p * bk);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int l = 0; l < D; ++l) acc += L.R[i * D + l] * ak[l];
+                    SL.ta[k][i] = acc * s;
+                }
+                // padding faces (k >= nr): never active, no contribution
+                SL.bD[k] = k < L.nr ? bk / a2 : T(0);
+                SL.w[k] = bk * SL.bD[k];
+                SL.ty[k] = k < L.nr ? T(0) : T(-3.0e38);
             }
-            SL.sl = lrec;
+            SL.rec = lrec;
         }
-        // SOLVER 1: the pair data of this warp's next obstacle are copied to
-        // shared memory asynchronously while the current obstacle is solved
-        auto prefetch = [&](int jn) {
+        // SOLVER 1: the pair data and halfspaces of this warp's next obstacle
+        // are copied to shared memory asynchronously while the current
+        // obstacle is solved (halfspaces into the other of the two buffers)
+        auto prefetch = [&](int jn, int buf) {
             if constexpr (SOLVER == 1) {
                 if (jn >= sm.M) return;
                 const int gmn = sm.obs0 + jn;
@@ -194,19 +208,22 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
                 cp_async_elem(pw + NY * 32, a.zeta + pn);
 #pragma unroll
                 for (int i = 0; i < D; ++i) cp_async_elem(pw + (NY + 1 + i) * 32, a.xi + (long long)i * P + pn);
-                // the obstacle's halfspaces, split over the lanes sharing them
+                // the obstacle's halfspaces, split over the lanes sharing them:
+                // normal m at [m * NC], offset m at [FO * NC + m]
+                T *obn = ob2 + buf * NOB;
                 const T *Cn = a.g.obs_C + (long long)gmn * FO * D;
                 const T *dn = a.g.obs_d + (long long)gmn * FO;
                 for (int e = g_r; e < non * (D + 1); e += g_n) {
-                    if (e < non * D) cp_async_elem(ob + e, Cn + e);
-                    else cp_async_elem(ob + FO * D + (e - non * D), dn + (e - non * D));
+                    if (e < non * D) cp_async_elem(obn + (e / D) * NC + e % D, Cn + e);
+                    else cp_async_elem(obn + FO * NC + (e - non * D), dn + (e - non * D));
                 }
                 cp_async_commit();
             }
         };
-        prefetch(j0);
+        prefetch(j0, 0);
 
-        for (int j = j0; j < sm.M; j += JS) {
+        int cnt = 0;  // obstacles of this sweep so far
+        for (int j = j0; j < sm.M; j += JS, ++cnt) {
             const int gm = sm.obs0 + j;
             L.C = a.g.obs_C + (long long)gm * FO * D;
             L.d = a.g.obs_d + (long long)gm * FO;
@@ -221,7 +238,11 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
                     for (int m = 0; m < L.no; ++m) y_out[(long long)(FR + m) * P + p] = y_in[(long long)(FR + m) * P + p];
                     y_out[(long long)(FR + FO) * P + p] = y_in[(long long)(FR + FO) * P + p];
                 }
-                prefetch(j + JS);  // nothing was copied for this obstacle: the buffers are free
+                // nothing was copied for this obstacle; the buffer the next copy
+                // fills was read by the previous obstacle's solve, which every
+                // sharing lane has finished once they meet here
+                if constexpr (SOLVER == 1) __syncwarp(gmask);
+                prefetch(j + JS, (cnt + 1) & 1);
                 continue;
             }
             T zeta, xi[D];
@@ -256,45 +277,39 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
             bool overflow = false;
             T lam_sum = T(0);
             if constexpr (SOLVER == 1) {
+                // a0 = sum lambda R a_k (world frame here); face records [d', iD, s, ybar]
+                const T *obc = ob2 + (cnt & 1) * NOB;
+                SL.nrm = obc;
+                // (lambda_k R a_k = prox w_k (lambda_k / bD_k) ta_k; ty_k = lambda_k / bD_k)
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     if (k < L.nr) {
-                        const T yv = pw[k * 32];
-                        SL.yl[k] = yv;
+                        const T tv = pw[k * 32] * m_rcp(SL.bD[k]);
+                        SL.ty[k] = tv;
 #pragma unroll
-                        for (int i = 0; i < D; ++i) a0[i] += yv * SL.a[k][i];
+                        for (int i = 0; i < D; ++i) a0[i] += (rho_p * SL.w[k] * tv) * SL.ta[k][i];
                     }
                 }
                 for (int m = 0; m < L.no; ++m) {
                     const T yv = pw[(FR + m) * 32];
                     T c[D], cr = T(0), c2 = T(0);
+                    nrm_load<T, D>(obc + m * NC, c);
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
-                        c[i] = ob[m * D + i];
                         w0[i] += yv * c[i];
                         cr += c[i] * L.rho[i];
                         c2 += c[i] * c[i];
                     }
-                    const T dm = ob[FO * D + m];
+                    const T dm = obc[FO * NC + m];
                     del0 += yv * dm;
                     const T dp = dm - cr;
-                    const T Dm = dp * dp + c2;
-                    const T iDm = m_rcp(rho_p * Dm);
-                    // body-frame normal c'_m = R^T c_m
-                    T cb[D];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        T acc = T(0);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * c[k];
-                        cb[i] = acc;
-                    }
-                    face_store<T, D>(lrec + m * FaceRec<D>::N, dp, iDm, yv, rho_p * Dm * yv * yv, cb);
+                    const T pD = rho_p * (dp * dp + c2);  // prox |K_m|^2
+                    rec_store<T>(lrec + 4 * m, dp, m_rcp(pD), yv * pD, yv);
                 }
                 SL.ybg = pw[(FR + FO) * 32];
                 del0 += SL.ybg;
-                __syncwarp(gmask);  // every sharing lane has read the halfspaces
-                prefetch(j + JS);   // the buffers are free again
+                __syncwarp(gmask);                 // every sharing lane has read the pair data
+                prefetch(j + JS, (cnt + 1) & 1);  // into the free buffers
             } else {
                 for (int g = 0; g < ng; ++g) {
                     const int c = g < L.nr ? g : (g < L.nr + L.no ? FR + g - L.nr : FR + FO);
@@ -335,11 +350,12 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
                 const T Tr = T(1) + del0 - wr;
                 zeta += Tr;
                 rp += double(Tr) * double(Tr);
+                // (SOLVER 1 holds A^T lambda rotated to the world frame: R^T (a0 + w0))
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    T acc = a0[i];
+                    T acc = SOLVER == 1 ? T(0) : a0[i];
 #pragma unroll
-                    for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * w0[k];
+                    for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * (SOLVER == 1 ? a0[k] + w0[k] : w0[k]);
                     xi[i] += acc;
                     rp += double(acc) * double(acc);
                 }
@@ -396,66 +412,75 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
                     }
                 }
             } else {
-                // ---- step 1 by semismooth Newton, warm-started at w0 = K^T y^j + bq
-                T ws[V];
+                // ---- step 1 by semismooth Newton in world coordinates (bqw = [bq0; R bq1]),
+                // warm-started at K^T y^j + bqw = [bq0 + del0 - rho.w0; R bq1 + a0 + w0]
+                T bqw[V], ws[V];
+                bqw[0] = bq[0];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc += L.R[i * D + k] * bq[1 + k];
+                    bqw[1 + i] = acc;
+                }
                 T wr = T(0);
 #pragma unroll
                 for (int i = 0; i < D; ++i) wr += w0[i] * L.rho[i];
-                ws[0] = bq[0] + del0 - wr;
+                ws[0] = bqw[0] + del0 - wr;
 #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    T acc = bq[1 + i] + a0[i];
-#pragma unroll
-                    for (int k = 0; k < D; ++k) acc += L.R[k * D + i] * w0[k];
-                    ws[1 + i] = acc;
-                }
+                for (int i = 0; i < D; ++i) ws[1 + i] = bqw[1 + i] + a0[i] + w0[i];
                 SL.no = L.no;
                 SsnKeep<T, NR> est;
-                status = ssn_solve_staged<T, D, NR>(SL, rho_p, irho, bq, ws, est);
+                status = ssn_solve_staged<T, D, NR>(SL, rho_p, irho, bqw, ws, est);
+                T a1w[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) a1w[i] = T(0);
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     if (k < L.nr) {
-                        const T yv = est.lam[k];
-                        const T dlt = yv - SL.yl[k];
+                        const T yv = SL.bD[k] * est.x[k];
+                        const T dlt = yv - SL.bD[k] * SL.ty[k];
                         dy2 += dlt * dlt;
                         yo[(long long)k * P] = yv;
 #pragma unroll
-                        for (int i = 0; i < D; ++i) a1[i] += yv * SL.a[k][i];
+                        for (int i = 0; i < D; ++i) a1w[i] += (rho_p * SL.w[k] * est.x[k]) * SL.ta[k][i];
                     }
                 }
-                // mu from the staged body-frame data; the sums sd = sum mu d',
-                // sc = sum mu c' give K^T y, and w1 = R sc, del1 = sd + rho.w1 + gamma
-                // the world-frame sums of the statistics
-                T sd = T(0), sc[D];
-#pragma unroll
-                for (int i = 0; i < D; ++i) sc[i] = T(0);
+                // mu at the solution from the staged records; the sums sd = sum mu d'
+                // and w1 = sum mu c (world frame) give K^T y and the statistics
+                T sd = T(0);
                 for (int m = 0; m < L.no; ++m) {
-                    T dp, iDm, ybm, sqm, c[D], cw = T(0);
-                    face_load<T, D>(lrec + m * FaceRec<D>::N, dp, iDm, ybm, sqm, c);
+                    T dp, iDm, s, ybm, c[D];
+                    rec_load<T>(lrec + 4 * m, dp, iDm, s, ybm);
+                    nrm_load<T, D>(SL.nrm + m * NC, c);
+                    T cw = T(0);
 #pragma unroll
                     for (int i = 0; i < D; ++i) cw += c[i] * ws[1 + i];
-                    const T yv = fmax(T(0), ybm - (ws[0] * dp + cw) * iDm);
+                    const T yv = fmax(T(0), (s - (ws[0] * dp + cw)) * iDm);
                     const T dlt = yv - ybm;
                     dy2 += dlt * dlt;
                     yo[(long long)(FR + m) * P] = yv;
                     sd += yv * dp;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) sc[i] += yv * c[i];
+                    for (int i = 0; i < D; ++i) w1[i] += yv * c[i];
                 }
                 const T gv = fmax(T(0), SL.ybg - ws[0] * irho);
                 yo[(long long)(FR + FO) * P] = gv;
-                // v = K^T y + bq from the written y
+                // v = K^T y + bq from the written y (body frame: R^T of the world sum)
+                // and A^T lambda in the body frame
                 v[0] = bq[0] + sd + gv;
-#pragma unroll
-                for (int i = 0; i < D; ++i) v[1 + i] = bq[1 + i] + a1[i] + sc[i];
                 T wr1 = T(0);
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    T acc = T(0);
+                    T acc = T(0), acc2 = T(0);
 #pragma unroll
-                    for (int k = 0; k < D; ++k) acc += L.R[i * D + k] * sc[k];
-                    w1[i] = acc;
-                    wr1 += acc * L.rho[i];
+                    for (int k = 0; k < D; ++k) {
+                        acc += L.R[k * D + i] * (a1w[k] + w1[k]);
+                        acc2 += L.R[k * D + i] * a1w[k];
+                    }
+                    v[1 + i] = bq[1 + i] + acc;
+                    a1[i] = acc2;
+                    wr1 += w1[i] * L.rho[i];
                 }
                 del1 = sd + wr1 + gv;
             }
@@ -476,36 +501,20 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
 #pragma unroll
                 for (int i = 0; i < D; ++i)
 #pragma unroll
-                    for (int jj = 0; jj <= i; ++jj) st_W[k++] += w1[i] * w1[jj];
+                    for (int jj = 0; jj <= i; ++jj, ++k) rsl[k * 32] += w1[i] * w1[jj];
 #pragma unroll
-                for (int i = 0; i < D; ++i) st_Wc[i] += cc * w1[i];
+                for (int i = 0; i < D; ++i) rsl[(NW + i) * 32] += cc * w1[i];
 #pragma unroll
                 for (int i = 0; i < D; ++i)
 #pragma unroll
-                    for (int jj = 0; jj < D; ++jj) st_E[i * D + jj] += w1[i] * e[jj];
+                    for (int jj = 0; jj < D; ++jj) rsl[(NW + D + i * D + jj) * 32] += w1[i] * e[jj];
             }
         }
     }
     if (MODE == 1) {
         // ---- reduce statistics and residual partials across the W warps
+        // (and, in a split tile, across the two half-warps of the same columns)
         T *rs = red;  // [W][NSTAT][32]
-        if (do_qp && split) {
-            // the upper half's statistics belong to the same columns as the lower half's
-#pragma unroll
-            for (int k = 0; k < NW; ++k) st_W[k] += __shfl_down_sync(0xffffffffu, st_W[k], 16);
-#pragma unroll
-            for (int k = 0; k < D; ++k) st_Wc[k] += __shfl_down_sync(0xffffffffu, st_Wc[k], 16);
-#pragma unroll
-            for (int k = 0; k < D * D; ++k) st_E[k] += __shfl_down_sync(0xffffffffu, st_E[k], 16);
-        }
-        if (do_qp) {
-#pragma unroll
-            for (int k = 0; k < NW; ++k) rs[(warp * NSTAT + k) * 32 + lane] = st_W[k];
-#pragma unroll
-            for (int k = 0; k < D; ++k) rs[(warp * NSTAT + NW + k) * 32 + lane] = st_Wc[k];
-#pragma unroll
-            for (int k = 0; k < D * D; ++k) rs[(warp * NSTAT + NW + D + k) * 32 + lane] = st_E[k];
-        }
         double *rr = reinterpret_cast<double *>(red + (size_t)W * NSTAT * 32);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -520,7 +529,10 @@ __global__ void __launch_bounds__(PairBound<D>::threads, OCA_PAIR_MIN_BLOCKS) k_
         if (do_qp && valid && hh == 0) {
             for (int k = warp; k < NSTAT; k += W) {
                 T acc = T(0);
-                for (int w2 = 0; w2 < W; ++w2) acc += rs[(w2 * NSTAT + k) * 32 + lane];
+                for (int w2 = 0; w2 < W; ++w2) {
+                    acc += rs[(w2 * NSTAT + k) * 32 + lane];
+                    if (split) acc += rs[(w2 * NSTAT + k) * 32 + lane + 16];
+                }
                 a.stats[(long long)k * a.Qtot + sm.qbeg + q] = acc;
             }
         }
@@ -733,15 +745,19 @@ cudaError_t launch_pose(const PoseArgs<T> &a, int maxQ, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-int pair_max_warps(int dim) { return (dim == 2 ? PairBound<2>::threads : PairBound<3>::threads) / 32; }
+int pair_max_warps(int dim, size_t es) {
+    const int t = dim == 3 ? (es == 4 ? PairBound<float, 3>::threads : PairBound<double, 3>::threads)
+                           : (es == 4 ? PairBound<float, 2>::threads : PairBound<double, 2>::threads);
+    return t / 32;
+}
 
 size_t pair_smem_bytes(int dim, size_t es, int W, int mode, int solver, int FR, int FO) {
     const int nstat = dim * (dim + 1) / 2 + dim + dim * dim;
     size_t b = 0;
     if (solver == 1) {
-        const size_t ls = dim == 2 ? (es == 4 ? face_lane_stride<float, 2>(FO) : face_lane_stride<double, 2>(FO))
-                                   : (es == 4 ? face_lane_stride<float, 3>(FO) : face_lane_stride<double, 3>(FO));
-        b += ls * 32 * W * es + (size_t)W * (FR + FO + 2 + dim) * 32 * es + (size_t)W * 2 * FO * (dim + 1) * es;
+        const size_t ls = es == 4 ? face_lane_stride<float>(FO) : face_lane_stride<double>(FO);
+        const size_t nob = dim == 2 ? obs_buf_elems<2>(FO) : obs_buf_elems<3>(FO);
+        b += ls * 32 * W * es + (size_t)W * (FR + FO + 2 + dim) * 32 * es + (size_t)W * 4 * nob * es;
     }
     if (mode == 1) b += (size_t)W * nstat * 32 * es + (size_t)W * 2 * sizeof(double);
     return b;

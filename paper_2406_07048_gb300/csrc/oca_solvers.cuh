@@ -844,121 +844,199 @@ OCA_HD inline T ssn_value(const Lane<T, D> &L, const T *ybar, long long P, int F
 }
 
 // ============================================================================
-// Semismooth Newton with staged generator data (the form the pair kernel
-// runs).  Per pair, the robot faces live in registers and the obstacle
-// faces' body-frame offsets d'_m, proximal reciprocals 1/(rho |K_m|^2),
-// previous values ybar_m and constants rho |K_m|^2 ybar_m^2 are staged once
-// in shared memory (lane-major: element m of thread tid at [m * BT + tid]),
-// so that each evaluation of y(w) costs one pass of multiply-adds over the
-// faces with no division.  Same mathematics as ssn_eval/ssn_solve above.
+// Semismooth Newton with staged face records (the form the pair kernel runs).
+//
+// The dual variable is carried in world coordinates, w = [w0; u] with
+// u = R w1 (w1 the body-frame part of ssn_solve's variable, R the part's
+// rotation).  R is orthogonal, so this is ssn_solve's iteration rotated:
+// every generator becomes a world-frame vector -- robot face k: [0; R a_k],
+// obstacle face m: [d'_m; c_m] with d'_m = d_m - c_m.rho, slack: [1; 0] --
+// and bq = [1 + zeta; R xi].
+//
+// Per lane (one (part, t) column, fixed over the obstacle sweep) the rotated
+// robot normals and the robot constants sit in registers.  Per pair, each
+// obstacle face is staged once as the record [d'_m, iD_m, s_m, ybar_m] with
+// iD_m = 1 / (prox |K_m|^2) and s_m = ybar_m prox |K_m|^2, and its world
+// normal c_m is read from the warp's shared copy of the obstacle's
+// halfspaces; an evaluation of y(w) is one pass of multiply-adds over the
+// faces: h_m = w0 d'_m + c_m.u, mu_m = max(0, (s_m - h_m) iD_m).
+//
+// Up to a constant independent of w, the dual function is
+//   psi(w) = 0.5 |w|^2 - bq.w + 0.5 sum_m mu_m^2 / iD_m + 0.5 prox gamma^2
+//            + 0.5 sum_k prox |a_k|^2 lambda_k^2 + prox tau
+// (a face's minimum over y >= 0 of h y + 0.5 prox |K|^2 (y - ybar)^2 is
+// 0.5 prox |K|^2 (ybar^2 - mu^2); the robot faces' minimum over
+// {lambda >= 0, b.lambda = 1}, with prox tau the multiplier of the equality,
+// is sum_k 0.5 prox |a_k|^2 (ybar_k^2 - lambda_k^2) - prox tau), and its
+// gradient is F(w) = w - bq - K^T y(w).  psi is convex and piecewise
+// quadratic: where the sets of positive lambda, mu and gamma are fixed, F is
+// affine with Jacobian H / prox.  A full Newton step from w whose end point
+// has the same sets as w therefore lands on the root of F (up to rounding),
+// and the solve stops there.
 // ============================================================================
+
+// One staged obstacle face of one lane: [d'_m, iD_m, s_m, ybar_m], 16-byte
+// aligned (FP32) or 32-byte (FP64).  A lane's records are contiguous; lanes
+// are face_lane_stride elements apart, an odd number of 16-byte units, so
+// that the eight lanes of each phase of a 16-byte shared load hit distinct
+// banks.
+template <typename T>
+OCA_HD inline int face_lane_stride(int FO) {
+    return sizeof(T) == 4 ? 4 * (FO | 1) : 4 * FO + 2;
+}
+// Normals of an obstacle in the warp's shared buffer: D values per face,
+// padded to NrmStride (2 in 2-D, 4 in 3-D) for aligned vector loads; the D
+// offsets d_m follow the FO normals.
+template <int D>
+struct NrmStride {
+    static constexpr int N = D == 2 ? 2 : 4;
+};
+// Elements of one obstacle's buffer, rounded up to 4 (16-byte alignment in
+// FP32, 32-byte in FP64).
+template <int D>
+OCA_HD inline int obs_buf_elems(int FO) {
+    return (FO * (NrmStride<D>::N + 1) + 3) & ~3;
+}
+
+template <typename T>
+OCA_HD inline void rec_load(const T *r, T &dp, T &iD, T &s, T &yb) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(r);
+        dp = v.x;
+        iD = v.y;
+        s = v.z;
+        yb = v.w;
+    } else {
+        const double2 v0 = *reinterpret_cast<const double2 *>(r);
+        const double2 v1 = *reinterpret_cast<const double2 *>(r + 2);
+        dp = v0.x;
+        iD = v0.y;
+        s = v1.x;
+        yb = v1.y;
+    }
+#else
+    dp = r[0];
+    iD = r[1];
+    s = r[2];
+    yb = r[3];
+#endif
+}
+// the first two fields only (the Hessian's pass over the active faces)
+template <typename T>
+OCA_HD inline void rec_load2(const T *r, T &dp, T &iD) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = *reinterpret_cast<const float2 *>(r);
+        dp = v.x;
+        iD = v.y;
+    } else {
+        const double2 v = *reinterpret_cast<const double2 *>(r);
+        dp = v.x;
+        iD = v.y;
+    }
+#else
+    dp = r[0];
+    iD = r[1];
+#endif
+}
+template <typename T>
+OCA_HD inline void rec_store(T *r, T dp, T iD, T s, T yb) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(r) = make_float4(dp, iD, s, yb);
+    } else {
+        *reinterpret_cast<double2 *>(r) = make_double2(dp, iD);
+        *reinterpret_cast<double2 *>(r + 2) = make_double2(s, yb);
+    }
+#else
+    r[0] = dp;
+    r[1] = iD;
+    r[2] = s;
+    r[3] = yb;
+#endif
+}
+template <typename T, int D>
+OCA_HD inline void nrm_load(const T *p, T (&c)[D]) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4 && D == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        c[0] = v.x;
+        c[1] = v.y;
+        return;
+    } else if constexpr (sizeof(T) == 4 && D == 3) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        c[0] = v.x;
+        c[1] = v.y;
+        c[2] = v.z;
+        return;
+    } else {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        c[0] = v.x;
+        c[1] = v.y;
+        if constexpr (D == 3) c[2] = p[2];
+    }
+#else
+#pragma unroll
+    for (int i = 0; i < D; ++i) c[i] = p[i];
+#endif
+}
+OCA_HD inline int low_bit(unsigned x) {
+#ifdef __CUDA_ARCH__
+    return __ffs(x) - 1;
+#else
+    return __builtin_ctz(x);
+#endif
+}
+
 template <typename T, int D, int NR>
 struct SsnLane {
-    // robot part
+    // robot part (per lane).  With n_k = |a_k|^2, the lambda subproblem is
+    // written in its breakpoints t_k = ty_k - ta_k.u: lambda_k = bD_k max(0, t_k - tau)
+    // and sum_k w_k max(0, t_k - tau) = 1 (sum b lambda = 1), where
+    // Faces k >= nr are padding with ta = 0, w = bD = 0 and ty = -3e38: their
+    // breakpoint never exceeds tau, so they are never active and add nothing.
     int nr;
-    T a[NR][D], b[NR];
-    T iDr[NR];   // 1 / (rho |a_k|^2)
-    T Db[NR];    // |a_k|^2 / b_k        (breakpoint scale)
-    T bD[NR];    // b_k / |a_k|^2
-    T b2D[NR];   // b_k^2 / |a_k|^2
-    T rD[NR];    // rho |a_k|^2
-    T iD[NR];    // 1 / |a_k|^2
-    T yl[NR];    // previous lambda
-    // obstacle faces, staged per lane in shared memory: record m at sl[m * kFaceRec]
-    // holds d'_m, 1 / (rho |K_m|^2), the previous mu_m, rho |K_m|^2 mu_m^2 and the
-    // body-frame normal c'_m = R^T c_m (FaceRec below)
+    T ta[NR][D];  // R a_k / (prox b_k)
+    T w[NR];      // b_k^2 / n_k
+    T bD[NR];     // b_k / n_k
+    T ty[NR];     // ybar_k n_k / b_k: the previous lambda (per pair)
+    // obstacle faces (per pair): this lane's staged records and the warp's
+    // world-frame normals, stride NrmStride<D>::N
     int no;
-    const T *sl;
+    const T *rec;
+    const T *nrm;
     // slack
     T ybg;
 };
 
-// One staged obstacle face of one lane: [d', 1/(rho |K|^2), mu^k, rho |K|^2 (mu^k)^2,
-// c'_0 .. c'_{D-1}], padded to an even length so that a lane's records can be
-// read as 8-byte pairs.  A lane's records are contiguous; lanes are
-// face_lane_stride elements apart, an odd number of 8-byte units, so that
-// the lanes of a half-warp reading the same field hit distinct banks.
-template <int D>
-struct FaceRec {
-    static constexpr int N = (4 + D + 1) & ~1;
-};
-template <typename T, int D>
-OCA_HD inline int face_lane_stride(int FO) {
-    return FaceRec<D>::N * FO + (sizeof(T) == 4 ? 2 : 1);
-}
-template <typename T, int D>
-OCA_HD inline void face_load(const T *r, T &dp, T &iD, T &yb, T &sq, T (&c)[D]) {
-#ifdef __CUDA_ARCH__
-    if constexpr (sizeof(T) == 4) {
-        const float2 a = *reinterpret_cast<const float2 *>(r);
-        const float2 b = *reinterpret_cast<const float2 *>(r + 2);
-        const float2 e = *reinterpret_cast<const float2 *>(r + 4);
-        dp = a.x;
-        iD = a.y;
-        yb = b.x;
-        sq = b.y;
-        c[0] = e.x;
-        c[1] = e.y;
-        if constexpr (D == 3) c[2] = r[6];
-        return;
-    }
-#endif
-    dp = r[0];
-    iD = r[1];
-    yb = r[2];
-    sq = r[3];
-#pragma unroll
-    for (int i = 0; i < D; ++i) c[i] = r[4 + i];
-}
-template <typename T, int D>
-OCA_HD inline void face_store(T *r, T dp, T iD, T yb, T sq, const T (&c)[D]) {
-#ifdef __CUDA_ARCH__
-    if constexpr (sizeof(T) == 4) {
-        *reinterpret_cast<float2 *>(r) = make_float2(dp, iD);
-        *reinterpret_cast<float2 *>(r + 2) = make_float2(yb, sq);
-        if constexpr (D == 2) {
-            *reinterpret_cast<float2 *>(r + 4) = make_float2(c[0], c[1]);
-        } else {
-            *reinterpret_cast<float2 *>(r + 4) = make_float2(c[0], c[1]);
-            r[6] = c[2];
-        }
-        return;
-    }
-#endif
-    r[0] = dp;
-    r[1] = iD;
-    r[2] = yb;
-    r[3] = sq;
-#pragma unroll
-    for (int i = 0; i < D; ++i) r[4 + i] = c[i];
-}
-
 template <typename T, int D, int NR>
 struct SsnEval {
-    T lam[NR];
+    T x[NR];         // max(0, t_k - tau): lambda_k = bD_k x_k
     T Kty[D + 1];
     T psi, pmag, mag;
-    T H[D + 1][D + 1];
+    unsigned fmask;  // obstacle faces with mu_m > 0
+    int amask;       // robot faces with lambda_k > 0
+    bool gact;       // gamma > 0
 };
 
 template <typename T, int D, int NR>
 OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, const T bq[D + 1], const T w[D + 1],
-                                   int &amask, SsnEval<T, D, NR> &st) {
-    // amask: in, the robot faces active at the previous evaluation (or at the
+                                   int &ahint, SsnEval<T, D, NR> &st) {
+    // ahint: in, the robot faces active at the previous evaluation (or at the
     // warm start); out, those active at w
-    constexpr int V = D + 1;
-    // lambda: z_k = ybar_k - a_k.w1 / (rho |a_k|^2), breakpoints t_k = z_k |a_k|^2 / b_k
-    T z[NR], t[NR], h[NR];
+    constexpr int V = D + 1, NC = NrmStride<D>::N;
+    // breakpoints t_k = ty_k - ta_k.u (prox b_k ta_k = R a_k, so ta_k.u = h_k / (prox b_k))
+    T t[NR], hh[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         T hk = T(0);
 #pragma unroll
-        for (int i = 0; i < D; ++i) hk += L.a[k][i] * w[1 + i];
-        h[k] = hk;
-        z[k] = L.yl[k] - hk * L.iDr[k];
-        t[k] = k < L.nr ? z[k] * L.Db[k] : T(-3.0e38);
+        for (int i = 0; i < D; ++i) hk += L.ta[k][i] * w[1 + i];
+        hh[k] = hk;
+        t[k] = L.ty[k] - hk;
     }
-    // threshold tau: on the active set {t_j > tau}, sum b z - tau sum b^2/D = 1.
+    // threshold tau: on the active set {t_j > tau}, sum w t - tau sum w = 1.
     // The previous active set is tried first: it is the answer when its tau
     // separates it from the other breakpoints (t_k > tau exactly on the set).
     // Otherwise the full search: the active set is the largest {t_j >= t_k}
@@ -967,16 +1045,16 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
     T bs1 = T(0), bs2 = T(0);
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-        if (k < L.nr && ((amask >> k) & 1)) {
-            bs1 += L.b[k] * z[k];
-            bs2 += L.b2D[k];
+        if ((ahint >> k) & 1) {
+            bs1 += L.w[k] * t[k];
+            bs2 += L.w[k];
         }
     bool hit = bs2 > T(0);
-    T inv = T(1) / (hit ? bs2 : T(1));
+    T inv = m_rcp(hit ? bs2 : T(1));
     T tau = (bs1 - T(1)) * inv;
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-        if (k < L.nr) hit = hit && ((((amask >> k) & 1) != 0) == (t[k] > tau));
+        hit = hit && ((((ahint >> k) & 1) != 0) == (t[k] > tau));
     if (!hit) {
         bs1 = T(1);
         bs2 = T(1);
@@ -987,108 +1065,69 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
             int n = 0;
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                if (j < L.nr && t[j] >= t[k]) {
-                    s1 += L.b[j] * z[j];
-                    s2 += L.b2D[j];
+                if (t[j] >= t[k]) {
+                    s1 += L.w[j] * t[j];
+                    s2 += L.w[j];
                     ++n;
                 }
             }
-            if (k < L.nr && s1 - T(1) < t[k] * s2 && n > best_n) {
+            if (s1 - T(1) < t[k] * s2 && n > best_n) {
                 best_n = n;
                 bs1 = s1;
                 bs2 = s2;
             }
         }
-        inv = T(1) / bs2;
-        tau = (bs1 - T(1)) * inv;  // 0 when no candidate qualified
+        inv = m_rcp(bs2);
+        tau = (bs1 - T(1)) * inv;
     }
-    T half_pen = T(0), lin = T(0), lmag = T(0), mag = T(0);
-    T a1[D], sc[D], sd = T(0);
+    // lambda_k = bD_k x_k with x_k = max(0, t_k - tau); prox n_k lambda_k^2 = prox w_k x_k^2;
+    // sum lambda_k R a_k = prox sum w_k x_k ta_k
+    T a1[D], rpen = T(0), rmag = T(0), mag = T(0);
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        a1[i] = T(0);
-        sc[i] = T(0);
-    }
-    T Ha[D][D], ba[D], bb = T(0);
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        ba[i] = T(0);
-#pragma unroll
-        for (int j = 0; j < D; ++j) Ha[i][j] = T(0);
-    }
-#pragma unroll
+    for (int i = 0; i < D; ++i) a1[i] = T(0);
     int nmask = 0;
+#pragma unroll
     for (int k = 0; k < NR; ++k) {
-        const T lk = k < L.nr ? fmax(T(0), z[k] - tau * L.bD[k]) : T(0);
-        st.lam[k] = lk;
-        nmask |= (lk > T(0) ? 1 : 0) << k;
-        if (k < L.nr) {
-            const T dl = lk - L.yl[k];
-            half_pen += T(0.5) * L.rD[k] * dl * dl;
-            lin += h[k] * lk;
-            lmag += m_abs(h[k] * lk);
-            mag += lk;
+        const T xk = fmax(T(0), t[k] - tau);
+        const T wx = L.w[k] * xk;
+        st.x[k] = xk;
+        nmask |= (xk > T(0) ? 1 : 0) << k;
+        rpen += wx * xk;
+        rmag += wx * (m_abs(L.ty[k]) + m_abs(hh[k]));
+        mag += L.bD[k] * xk;
 #pragma unroll
-            for (int i = 0; i < D; ++i) a1[i] += lk * L.a[k][i];
-            if (lk > T(0)) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    ba[i] += L.b[k] * L.a[k][i] * L.iD[k];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) Ha[i][j] += L.a[k][i] * L.a[k][j] * L.iD[k];
-                }
-                bb += L.b2D[k];
-            }
-        }
+        for (int i = 0; i < D; ++i) a1[i] += wx * L.ta[k][i];
     }
-    // faces: h_m = w0 d'_m + c'_m.w1 (body frame), mu_m = max(0, ybar_m - h_m / (rho |K_m|^2))
-    // M = sum_active [d'; c'][d'; c']^T / |K_m|^2
-    T Mp[V][V];
 #pragma unroll
-    for (int i = 0; i < V; ++i)
+    for (int i = 0; i < D; ++i) a1[i] *= rho_p;
+    // faces: mu_m = max(0, (s_m - h_m) iD_m); penalty mu_m (s_m - h_m) = mu_m^2 / iD_m
+    // Rounding scales: a term mu r (r = s - h > 0 where mu > 0) is computed
+    // from s and h with |h| <= s + r, so sum mu (s + |h|) <= 2 sum mu s + fpen
+    // bounds the magnitudes that enter psi; sum mu (|d'| + 1) those of the
+    // face part of K^T y (unit-scale normals).
+    T fpen = T(0), fms = T(0), sd = T(0), sc[D];
 #pragma unroll
-        for (int j = 0; j < V; ++j) Mp[i][j] = T(0);
-    // proximal terms of the faces, doubled: rho |K|^2 (mu - ybar)^2; an
-    // inactive face (mu_m = 0) contributes its constant rho |K|^2 ybar^2 only
-    T face_pen = T(0);
+    for (int i = 0; i < D; ++i) sc[i] = T(0);
+    unsigned fmask = 0u;
     for (int m = 0; m < L.no; ++m) {
-        T dp, iDm, yb, sqm, c[D], cw = T(0);
-        face_load<T, D>(L.sl + m * FaceRec<D>::N, dp, iDm, yb, sqm, c);
+        T dp, iDm, s, yb, c[D];
+        rec_load<T>(L.rec + 4 * m, dp, iDm, s, yb);
+        nrm_load<T, D>(L.nrm + NC * m, c);
+        T cw = T(0);
 #pragma unroll
         for (int i = 0; i < D; ++i) cw += c[i] * w[1 + i];
-        const T hm = w[0] * dp + cw;
-        const T mu = yb - hm * iDm;
-        if (mu > T(0)) {
-            face_pen += hm * hm * iDm;     // mu - ybar = -h iD
-            const T wgt = rho_p * iDm;     // 1 / |K_m|^2
-            T e[V];
-            e[0] = dp;
+        const T r = s - (w[0] * dp + cw);
+        T mu = r * iDm;
+        fmask |= (mu > T(0) ? 1u : 0u) << m;
+        mu = fmax(mu, T(0));
+        fpen += mu * r;
+        fms += mu * s;
+        mag += mu * (m_abs(dp) + T(1));
+        sd += mu * dp;
 #pragma unroll
-            for (int i = 0; i < D; ++i) e[1 + i] = c[i];
-            T we[V];
-#pragma unroll
-            for (int i = 0; i < V; ++i) we[i] = wgt * e[i];
-#pragma unroll
-            for (int i = 0; i < V; ++i)
-#pragma unroll
-                for (int j = 0; j <= i; ++j) Mp[i][j] += we[i] * e[j];
-            lin += hm * mu;
-            sd += mu * dp;
-#pragma unroll
-            for (int i = 0; i < D; ++i) sc[i] += mu * c[i];
-            lmag += (m_abs(w[0] * dp) + m_abs(cw)) * mu;
-            mag += mu * (m_abs(dp) + T(1));
-        } else {
-            face_pen += sqm;
-        }
+        for (int i = 0; i < D; ++i) sc[i] += mu * c[i];
     }
-    half_pen += T(0.5) * face_pen;
     const T gam = fmax(T(0), L.ybg - w[0] * irho);
-    {
-        const T dg = gam - L.ybg;
-        half_pen += T(0.5) * rho_p * dg * dg;
-    }
-    lin += w[0] * gam;
     st.Kty[0] = sd + gam;
 #pragma unroll
     for (int i = 0; i < D; ++i) st.Kty[1 + i] = a1[i] + sc[i];
@@ -1098,30 +1137,85 @@ OCA_HD inline void ssn_eval_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
         ww += w[i] * w[i];
         bw += bq[i] * w[i];
     }
-    st.psi = T(0.5) * ww - bw - (half_pen + lin);
+    const T gp = rho_p * gam * gam;
+    st.psi = T(0.5) * ww - bw + T(0.5) * (fpen + gp) + rho_p * (T(0.5) * rpen + tau);
+    st.pmag = T(0.5) * ww + m_abs(bw) + fms + fpen + T(0.5) * gp + rho_p * (rmag + T(2) * (m_abs(tau) + inv));
     st.mag = mag + gam;
-    st.pmag = T(0.5) * ww + m_abs(bw) + half_pen + lmag + m_abs(w[0] * gam);
-    // H = rho I + M + e0 e0^T [gamma active] + lambda part
-    amask = nmask;
-    // 1 / sum_active b^2/D: the threshold's denominator when the sets agree
-    const T ibb = bb > T(0) ? (bb == bs2 ? inv : T(1) / bb) : T(0);
+    st.fmask = fmask;
+    st.amask = nmask;
+    st.gact = gam > T(0);
+    ahint = nmask;
+}
+
+// H = prox I + sum_{mu_m > 0} K_m K_m^T / |K_m|^2 + e0 e0^T [gamma > 0]
+//     + (lambda block on u: sum_S a a^T/n - (sum_S b a/n)(...)^T / sum_S b^2/n
+//        = prox^2 (sum_S w ta ta^T - (sum_S w ta)(sum_S w ta)^T / sum_S w)),
+// over the sets of the evaluation st (world frame)
+template <typename T, int D, int NR>
+OCA_HD inline void ssn_hess_staged(const SsnLane<T, D, NR> &L, T rho_p, const SsnEval<T, D, NR> &st,
+                                   T H[D + 1][D + 1]) {
+    constexpr int V = D + 1, NC = NrmStride<D>::N;
+    T M[V][V];
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+#pragma unroll
+        for (int j = 0; j < V; ++j) M[i][j] = T(0);
+    for (unsigned fm = st.fmask; fm != 0u; fm &= fm - 1u) {
+        const int m = low_bit(fm);
+        T e[V], iDm;
+        rec_load2<T>(L.rec + 4 * m, e[0], iDm);
+        T c[D];
+        nrm_load<T, D>(L.nrm + NC * m, c);
+#pragma unroll
+        for (int i = 0; i < D; ++i) e[1 + i] = c[i];
+        T we[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) we[i] = iDm * e[i];
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) M[i][j] += we[i] * e[j];
+    }
+    T Ha[D][D], ba[D], bb = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        ba[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) Ha[i][j] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        if ((st.amask >> k) & 1) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const T ai = L.w[k] * L.ta[k][i];
+                ba[i] += ai;
+#pragma unroll
+                for (int j = 0; j <= i; ++j) Ha[i][j] += ai * L.ta[k][j];
+            }
+            bb += L.w[k];
+        }
+    }
+    const T ibb = bb > T(0) ? m_rcp(bb) : T(0);
+    const T r2 = rho_p * rho_p;
 #pragma unroll
     for (int i = 0; i < V; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
-            T hv = Mp[i][j] + (i == j ? rho_p : T(0));
-            if (i == 0 && j == 0 && gam > T(0)) hv += T(1);
-            if (i > 0 && j > 0) hv += Ha[i - 1][j - 1] - ba[i - 1] * ba[j - 1] * ibb;
-            st.H[i][j] = hv;
-            st.H[j][i] = hv;
+            T hv = rho_p * M[i][j] + (i == j ? rho_p : T(0));
+            if (i == 0 && j == 0 && st.gact) hv += T(1);
+            if (i > 0 && j > 0) hv += r2 * (Ha[i - 1][j - 1] - ba[i - 1] * ba[j - 1] * ibb);
+            H[i][j] = hv;
+            H[j][i] = hv;
         }
 }
 
 // The part of an evaluation the solve carries from one pass to the next:
-// the accepted point's lambda (the result), psi and its rounding scale.
+// the accepted point's x (lambda_k = bD_k x_k, the result), psi and its
+// rounding scale.
 template <typename T, int NR>
 struct SsnKeep {
-    T lam[NR];
+    T x[NR];
     T psi, pmag;
 };
 
@@ -1130,43 +1224,59 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
                                    SsnKeep<T, NR> &st) {
     // One loop with a single evaluation site: every pass evaluates y(w) at
     // one point -- the start point, or a trial w + t d of the line search --
-    // and then either backtracks, or accepts the trial and computes the next
-    // Newton direction from that evaluation.  (The same sequence of
-    // evaluations as a Newton loop with a nested line search; but the large
-    // evaluation code exists once, and lanes of a warp in different phases
-    // share evaluation passes.)
+    // and then stops (a full Newton step that stayed in the region of its
+    // Hessian), backtracks, or accepts the trial and computes the next Newton
+    // direction from that evaluation.  (The same sequence of evaluations as a
+    // Newton loop with a nested line search; but the evaluation code exists
+    // once, and lanes of a warp in different phases share evaluation passes.)
     constexpr int V = D + 1;
     int status = OCA_PAIR_ITER_CAP;
     T dlt[V], wt[V], tstep = T(1), gd = T(0);
-    bool started = false;
+    bool started = false, newton = false;
     int it = 0, ls = 0;
     // robot faces active at the last evaluation; first guess: the warm start's
-    int amask = 0;
+    int ahint = 0;
 #pragma unroll
-    for (int k = 0; k < NR; ++k) amask |= (k < L.nr && L.yl[k] > T(0) ? 1 : 0) << k;
+    for (int k = 0; k < NR; ++k) ahint |= (L.ty[k] > T(0) ? 1 : 0) << k;
+    // the sets at the point whose Hessian gave the current direction
+    unsigned hf = 0u;
+    int ha = 0;
+    bool hg = false;
     for (int pass = 0; pass < 1 + 60 * 30; ++pass) {
 #pragma unroll
         for (int i = 0; i < V; ++i) wt[i] = started ? w[i] + tstep * dlt[i] : w[i];
         SsnEval<T, D, NR> trial;
-        ssn_eval_staged<T, D, NR>(L, rho_p, irho, bq, wt, amask, trial);
+        ssn_eval_staged<T, D, NR>(L, rho_p, irho, bq, wt, ahint, trial);
         bool stop = false;
         if (started) {
-            const bool ok = trial.psi <= st.psi + T(1e-4) * tstep * gd + T(8) * m_eps<T>() * (st.pmag + trial.pmag);
-            if (!ok && ls < 29) {
-                // backtracking on psi: psi is piecewise quadratic along the ray,
-                // so the minimiser of the quadratic through psi(0), psi'(0) = gd
-                // and psi(t) is usually exact after one rejected trial
-                const T curv = trial.psi - st.psi - tstep * gd;   // (psi(t) - psi(0) - t psi'(0)) = a t^2
-                T tn = curv > T(0) ? -gd * tstep * tstep / (T(2) * curv) : T(0.5) * tstep;
-                tstep = fmin(fmax(tn, T(0.1) * tstep), T(0.5) * tstep);
-                ++ls;
-                continue;
-            }
-            if (!ok) {
-                status = OCA_PAIR_OK;  // no decrease at rounding level
+            if (newton && tstep == T(1) && trial.fmask == hf && trial.amask == ha && trial.gact == hg) {
+                // F is affine between w and the trial: the Newton point is the root
+                status = OCA_PAIR_OK;
                 stop = true;
+            } else {
+                // Armijo decrease, relaxed by the rounding level of psi; psi may
+                // rise only when the predicted decrease is itself below that
+                // level (a rise above it, with a larger predicted decrease, is a
+                // real one: accepting it can cycle between two regions)
+                const T slack = T(8) * m_eps<T>() * (st.pmag + trial.pmag);
+                const bool ok = trial.psi <= st.psi + T(1e-4) * tstep * gd + slack &&
+                                (trial.psi <= st.psi || -tstep * gd <= slack);
+                if (!ok && ls < 29) {
+                    // backtracking on psi: psi is piecewise quadratic along the ray,
+                    // so the minimiser of the quadratic through psi(0), psi'(0) = gd
+                    // and psi(t) is usually exact after one rejected trial
+                    const T curv = trial.psi - st.psi - tstep * gd;
+                    T tn = curv > T(0) ? -gd * tstep * tstep / (T(2) * curv) : T(0.5) * tstep;
+                    tstep = fmin(fmax(tn, T(0.1) * tstep), T(0.5) * tstep);
+                    ++ls;
+                    continue;
+                }
+                if (!ok) {
+                    status = OCA_PAIR_OK;  // no decrease at rounding level
+                    stop = true;
+                }
+                if (++it >= 60) stop = true;
             }
-            if (++it >= 60) stop = true;
         } else {
             started = true;
         }
@@ -1174,7 +1284,7 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
 #pragma unroll
         for (int i = 0; i < V; ++i) w[i] = wt[i];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) st.lam[k] = trial.lam[k];
+        for (int k = 0; k < NR; ++k) st.x[k] = trial.x[k];
         st.psi = trial.psi;
         st.pmag = trial.pmag;
         if (stop) break;
@@ -1194,9 +1304,12 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
             status = OCA_PAIR_NONFINITE;
             break;
         }
+        T H[V][V];
+        ssn_hess_staged<T, D, NR>(L, rho_p, trial, H);
 #pragma unroll
         for (int i = 0; i < V; ++i) dlt[i] = -rho_p * F[i];
-        if (!chol_solve<T, V>(trial.H, dlt, V, T(0))) {
+        newton = chol_solve<T, V>(H, dlt, V, T(0));
+        if (!newton) {
 #pragma unroll
             for (int i = 0; i < V; ++i) dlt[i] = -F[i];
         }
@@ -1209,7 +1322,11 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
             gd = T(0);
 #pragma unroll
             for (int i = 0; i < V; ++i) gd -= F[i] * F[i];
+            newton = false;
         }
+        hf = trial.fmask;
+        ha = trial.amask;
+        hg = trial.gact;
         tstep = T(1);
         ls = 0;
     }

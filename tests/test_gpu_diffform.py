@@ -120,6 +120,11 @@ def test_diffform_fp32_adjoint_matches_fp64_fd(B, ora):
                   f"{[float(a) for _, a in fds]}, replaced")
             continue
         scale_g = np.sqrt((g_d[j0:j1] ** 2).sum() + (g_c[j0:j1] ** 2).sum())
+        a, b = int(sc.state_begin[s]), int(sc.state_begin[s + 1])
+        s_o = r["s"][: b - a]
+        dev = np.abs(pb.s[a:b].double().cpu().numpy() - s_o).max() / (1.0 + np.abs(s_o).max())
+        print(f"[diffform scen {s} K={K}] FP32 forward vs FP64 oracle after K iterations: "
+              f"max state deviation {dev:.3g} (relative)")
         for (name, dd, ad), (fd, _) in zip(dirs, fds):
             err = abs(fd - ad) / (abs(fd) + 1e-3 * scale_g * np.linalg.norm(dd))
             worst = max(worst, err)
