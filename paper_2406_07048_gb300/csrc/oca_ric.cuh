@@ -364,6 +364,50 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
             if (e < NST) nxt[r] = ric_stage_elem<F, NS, NU>(scr, N, N - 1, e);
         }
     }
+    // each thread's entries of the stage matrix M (upper triangle row by row,
+    // then the gradient column) and of P (upper triangle, then p): their (i, j)
+    // depend on the thread only.  With NT > 32 (the 12-state model: 152 and 90
+    // entries per step) they are found once, before the steps; a one-warp group
+    // (27-35 entries) finds them in each step, which measured faster there.
+    constexpr bool HOIST = NT > 32;
+    constexpr int RM = HOIST ? (NSYM + NZ + NT - 1) / NT : 1, RP = HOIST ? (NPS + NS + NT - 1) / NT : 1;
+    int mi[RM], mj[RM], pi_[RP], pj[RP];
+    if constexpr (HOIST) {
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            const int e = lane + NT * r;
+            int i = 0, j = NZ;
+            if (e < NSYM) {
+                int rem = e;
+                while (rem >= NZ - i) {
+                    rem -= NZ - i;
+                    ++i;
+                }
+                j = i + rem;
+            } else {
+                i = e - NSYM;
+            }
+            mi[r] = i;
+            mj[r] = j;
+        }
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+            const int e = lane + NT * r;
+            int i = 0, j = NS;  // j = NS marks p_i
+            if (e < NPS) {
+                int rem = e;
+                while (rem >= NS - i) {
+                    rem -= NS - i;
+                    ++i;
+                }
+                j = i + rem;
+            } else {
+                i = e - NPS;
+            }
+            pi_[r] = i;
+            pj[r] = j;
+        }
+    }
     bool ok = true;
     for (int t = N - 1; t >= 0; --t) {
 #pragma unroll
@@ -389,6 +433,22 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
         }
         ric_sync<NT>();
         // M: the upper triangle of the Hessian part, then the gradient column
+        if constexpr (HOIST) {
+#pragma unroll
+            for (int r = 0; r < RM; ++r) {
+                if (lane + NT * r >= NSYM + NZ) break;
+                const int i = mi[r], j = mj[r];
+                const int jy = j < NZ ? j : NX - 1;
+                F acc;
+                if (j == NZ) acc = i < NS ? qs[i] : rs[i - NS];
+                else if (j < NS) acc = Qs[i * NS + j];
+                else acc = (i == j) ? ru_diag[i - NS] : F(0);
+#pragma unroll
+                for (int k = 0; k < NS; ++k) acc += Gs[k * NX + i] * Y[k * NX + jy];
+                M[i * MC + j] = acc;
+                if (j < NZ && j != i) M[j * MC + i] = acc;
+            }
+        } else
         for (int e = lane; e < NSYM + NZ; e += NT) {
             int i, j;
             if (e < NSYM) {
@@ -433,6 +493,25 @@ __device__ bool ric_factor(F *scr, int N, const F *ru_diag) {
         }
         ric_sync<NT>();
         // P_t = Qss + Qus^T K_t (upper triangle, mirrored), p_t = qs + Qus^T k_t
+        if constexpr (HOIST) {
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+                if (lane + NT * r >= NPS + NS) break;
+                const int i = pi_[r], j = pj[r];
+                if (j < NS) {
+                    F acc = M[i * MC + j];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) acc += M[(NS + a) * MC + i] * KK[a * (NS + 1) + j];
+                    P[i * NS + j] = acc;
+                    P[j * NS + i] = acc;
+                } else {
+                    F acc = M[i * MC + NZ];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) acc += M[(NS + a) * MC + i] * KK[a * (NS + 1) + NS];
+                    pv[i] = acc;
+                }
+            }
+        } else
         for (int e = lane; e < NPS + NS; e += NT) {
             if (e < NPS) {
                 int rem = e, i = 0;
