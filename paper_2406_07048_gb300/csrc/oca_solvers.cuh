@@ -794,7 +794,8 @@ OCA_HD inline int ssn_solve(const Lane<T, D> &L, const T *ybar, long long P, int
 #pragma unroll
             for (int i = 0; i < V; ++i) wt[i] = w[i] + t * dlt[i];
             ssn_eval<T, D>(L, ybar, P, FR, FO, rho_p, bq, wt, true, trial);
-            if (trial.psi <= st.psi + T(1e-4) * t * gd + T(8) * m_eps<T>() * (st.pmag + trial.pmag)) {
+            const T slack = T(8) * m_eps<T>() * (st.pmag + trial.pmag);
+            if (trial.psi <= st.psi + T(1e-4) * t * gd + slack && (trial.psi < st.psi || -t * gd <= slack)) {
                 ok = true;
                 break;
             }
@@ -1254,13 +1255,13 @@ OCA_HD inline int ssn_solve_staged(const SsnLane<T, D, NR> &L, T rho_p, T irho, 
                 status = OCA_PAIR_OK;
                 stop = true;
             } else {
-                // Armijo decrease, relaxed by the rounding level of psi; psi may
-                // rise only when the predicted decrease is itself below that
-                // level (a rise above it, with a larger predicted decrease, is a
-                // real one: accepting it can cycle between two regions)
+                // Armijo decrease, relaxed by the rounding level of psi; psi must
+                // strictly decrease unless the predicted decrease is itself below
+                // that level (a tie or a rise with a larger predicted decrease is
+                // real: accepting it can cycle between two regions)
                 const T slack = T(8) * m_eps<T>() * (st.pmag + trial.pmag);
                 const bool ok = trial.psi <= st.psi + T(1e-4) * tstep * gd + slack &&
-                                (trial.psi <= st.psi || -tstep * gd <= slack);
+                                (trial.psi < st.psi || -tstep * gd <= slack);
                 if (!ok && ls < 29) {
                     // backtracking on psi: psi is piecewise quadratic along the ray,
                     // so the minimiser of the quadratic through psi(0), psi'(0) = gd
