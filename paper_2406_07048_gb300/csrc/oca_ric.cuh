@@ -274,7 +274,12 @@ template <typename F, int NU>
 __device__ __forceinline__ bool spd_inverse(const F (&U)[NU][NU], F (&X)[NU][NU]) {
     if constexpr (NU == 2) {
         const F det = U[0][0] * U[1][1] - U[0][1] * U[0][1];
-        if (!(U[0][0] > F(0)) || !(det > F(0))) return false;
+        if (!(U[0][0] > F(0)) || !(det > F(0))) {
+            // not positive definite: X = 0 (the gains of this stage vanish; the
+            // caller reports the failure), never values left from before
+            X[0][0] = X[0][1] = X[1][0] = X[1][1] = F(0);
+            return false;
+        }
         const F id = F(1) / det;
         X[0][0] = U[1][1] * id;
         X[1][1] = U[0][0] * id;
